@@ -1,0 +1,434 @@
+/*
+ * CPU ORACLE for canonical 2-hop distance labeling -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may load this library.  The GPU library shares no code with it.
+ *
+ * Plain, sequential, obviously-correct restatements of the paper
+ * ("Pruned Landmark Labeling Meets Vertex Centric Computation", Jin et al.):
+ *
+ *   oracle_pll      Alg. 1 (PLL, Sec. 2.1.1): one pruned BFS per root in rank
+ *                   order, with the "small revision" (a root is only pushed to
+ *                   neighbours it outranks).  The pruning test uses an array
+ *                   map of L(u) (Sec. 3.3, cost discussion).
+ *   oracle_vcpll    Alg. 3 (VC-PLL, Sec. 3.1): all vertices spread at once,
+ *                   one scatter/gather round per distance; unique messages;
+ *                   distance check against the labels of the previous round.
+ *   oracle_chhl_row Def. 2 (canonical hierarchical hub labeling) for one
+ *                   vertex: h is a hub of v iff h has the highest rank in
+ *                   P_hv, the set of vertices on all shortest h-v paths.
+ *                   One BFS from v; m(x) = best rank over P_vx is carried
+ *                   along the BFS DAG.
+ *   oracle_query    2-hop query (Sec. 2.1): min over common hubs of
+ *                   d(u,h) + d(h,v), by a merge of two hub-sorted lists;
+ *                   -1 when no hub is common (different components).
+ *   oracle_bfs      textbook BFS distances (-1 unreachable).
+ *
+ * Conventions: vertices are original ids 0..n-1; the order is given as
+ * order[r] = id of rank r (rank 0 = highest); label entries store the hub as
+ * its RANK (uint32) and the distance (uint8); each label row is sorted by hub
+ * rank ascending.  Readings where the paper is silent: unreachable -> -1;
+ * a tie in the distance check prunes (the paper's test is strict "<").
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    uint32_t* hub;
+    uint8_t* dist;
+    int64_t len, cap;
+} row_t;
+
+typedef struct {
+    int64_t n;
+    row_t* rows;
+    int64_t total;
+    int32_t max_dist;
+    int32_t rounds;          /* VC-PLL only */
+    int64_t stats[4 * 256];  /* VC-PLL per round: messages, unique, accepted, checks */
+} labels_t;
+
+static int row_push(row_t* r, uint32_t h, uint8_t d) {
+    if (r->len == r->cap) {
+        int64_t nc = r->cap ? 2 * r->cap : 4;
+        uint32_t* nh = (uint32_t*)realloc(r->hub, sizeof(uint32_t) * (size_t)nc);
+        if (!nh) return -1;
+        r->hub = nh;
+        uint8_t* nd = (uint8_t*)realloc(r->dist, (size_t)nc);
+        if (!nd) return -1;
+        r->dist = nd;
+        r->cap = nc;
+    }
+    r->hub[r->len] = h;
+    r->dist[r->len] = d;
+    r->len++;
+    return 0;
+}
+
+static labels_t* labels_new(int64_t n) {
+    labels_t* L = (labels_t*)calloc(1, sizeof(labels_t));
+    L->n = n;
+    L->rows = (row_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(row_t));
+    return L;
+}
+
+void oracle_labels_free(void* h) {
+    labels_t* L = (labels_t*)h;
+    if (!L) return;
+    for (int64_t v = 0; v < L->n; ++v) {
+        free(L->rows[v].hub);
+        free(L->rows[v].dist);
+    }
+    free(L->rows);
+    free(L);
+}
+
+int64_t oracle_labels_total(void* h) { return ((labels_t*)h)->total; }
+int32_t oracle_labels_max_dist(void* h) { return ((labels_t*)h)->max_dist; }
+int32_t oracle_labels_rounds(void* h) { return ((labels_t*)h)->rounds; }
+const int64_t* oracle_labels_stats(void* h) { return ((labels_t*)h)->stats; }
+
+/* CSR export: off[n+1], hub[total], dist[total], rows by original id. */
+void oracle_labels_export(void* h, int64_t* off, uint32_t* hub, uint8_t* dist) {
+    labels_t* L = (labels_t*)h;
+    int64_t k = 0;
+    off[0] = 0;
+    for (int64_t v = 0; v < L->n; ++v) {
+        const row_t* r = &L->rows[v];
+        if (r->len) {
+            memcpy(hub + k, r->hub, sizeof(uint32_t) * (size_t)r->len);
+            memcpy(dist + k, r->dist, (size_t)r->len);
+        }
+        k += r->len;
+        off[v + 1] = k;
+    }
+}
+
+static void finish_totals(labels_t* L) {
+    L->total = 0;
+    L->max_dist = 0;
+    for (int64_t v = 0; v < L->n; ++v) {
+        L->total += L->rows[v].len;
+        for (int64_t i = 0; i < L->rows[v].len; ++i)
+            if (L->rows[v].dist[i] > L->max_dist) L->max_dist = L->rows[v].dist[i];
+    }
+}
+
+#define INF_D 0x7fffffff
+
+/* ----------------------------------------------------------------- Alg. 1 */
+/* Returns NULL on allocation failure or when a label distance exceeds 254. */
+void* oracle_pll(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order) {
+    labels_t* L = labels_new(n);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t* T = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));  /* hub rank -> d(u,hub) */
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));  /* BFS distance, -1 unvisited */
+    int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int fail = 0;
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t i = 0; i < n; ++i) {
+        T[i] = INF_D;
+        D[i] = -1;
+    }
+    for (int64_t r = 0; r < n && !fail; ++r) {           /* roots from high to low rank */
+        const int32_t u = order[r];
+        const row_t* Lu = &L->rows[u];
+        const int64_t lu_len = Lu->len;                  /* L(u) before this root */
+        for (int64_t i = 0; i < lu_len; ++i) T[Lu->hub[i]] = Lu->dist[i];
+        int64_t head = 0, tail = 0;
+        Q[tail++] = u;
+        D[u] = 0;
+        while (head < tail) {
+            const int32_t v = Q[head++];
+            const int32_t delta = D[v];
+            /* prune iff some common hub w gives T[w] + d(w,v) <= delta */
+            int pruned = 0;
+            const row_t* Lv = &L->rows[v];
+            for (int64_t i = 0; i < Lv->len; ++i) {
+                const int32_t tw = T[Lv->hub[i]];
+                if (tw != INF_D && tw + (int32_t)Lv->dist[i] <= delta) {
+                    pruned = 1;
+                    break;
+                }
+            }
+            if (pruned) continue;
+            if (delta > 254) {
+                fail = 1;
+                break;
+            }
+            if (row_push(&L->rows[v], (uint32_t)r, (uint8_t)delta)) {
+                fail = 1;
+                break;
+            }
+            for (int64_t j = off[v]; j < off[v + 1]; ++j) {
+                const int32_t w = col[j];
+                if (rank[w] > r && D[w] < 0) {           /* small revision */
+                    D[w] = delta + 1;
+                    Q[tail++] = w;
+                }
+            }
+        }
+        for (int64_t i = 0; i < tail; ++i) D[Q[i]] = -1;
+        for (int64_t i = 0; i < lu_len; ++i) T[L->rows[u].hub[i]] = INF_D;
+    }
+    free(rank);
+    free(T);
+    free(D);
+    free(Q);
+    if (fail) {
+        oracle_labels_free(L);
+        return NULL;
+    }
+    finish_totals(L);
+    return L;
+}
+
+/* ----------------------------------------------------------------- Alg. 3 */
+/* Round d: each v gathers (u, d) from every neighbour a with u in dL(a),
+ * rank(u) < rank(v) and u not in L(v); unique messages are checked against
+ * the labels as they stood after round d-1; the accepted ones form dL(v) and
+ * are added to L(v) after all vertices have been gathered. */
+void* oracle_vcpll(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order) {
+    labels_t* L = labels_new(n);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    row_t* dL = (row_t*)calloc(nn, sizeof(row_t));      /* new labels of the previous round (hub ranks) */
+    row_t* ndL = (row_t*)calloc(nn, sizeof(row_t));     /* new labels of this round */
+    int32_t* Tv = (int32_t*)malloc(sizeof(int32_t) * nn);  /* hub rank -> d(v,hub), L(v) as an array */
+    int32_t* seen = (int32_t*)malloc(sizeof(int32_t) * nn); /* message dedup stamp per hub rank */
+    int32_t* msgs = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int fail = 0;
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t i = 0; i < n; ++i) {
+        Tv[i] = INF_D;
+        seen[i] = -1;
+    }
+    /* Init: dL(v) = L(v) = {(v, 0)} */
+    for (int64_t v = 0; v < n; ++v) {
+        row_push(&L->rows[v], (uint32_t)rank[v], 0);
+        row_push(&dL[v], (uint32_t)rank[v], 0);
+    }
+    int32_t d = 0;
+    int64_t active = n;
+    while (active > 0 && !fail) {
+        ++d;
+        int64_t st_msgs = 0, st_unique = 0, st_acc = 0, st_checks = 0;
+        active = 0;
+        for (int64_t v = 0; v < n; ++v) {                 /* gather at v */
+            const row_t* Lv = &L->rows[v];
+            for (int64_t i = 0; i < Lv->len; ++i) Tv[Lv->hub[i]] = Lv->dist[i];
+            int64_t nm = 0;
+            for (int64_t j = off[v]; j < off[v + 1]; ++j) {
+                const row_t* da = &dL[col[j]];
+                for (int64_t i = 0; i < da->len; ++i) {
+                    const uint32_t u = da->hub[i];       /* rank of u */
+                    if ((int64_t)u < (int64_t)rank[v] && Tv[u] == INF_D) {
+                        ++st_msgs;
+                        if (seen[u] != (int32_t)v) {
+                            seen[u] = (int32_t)v;
+                            msgs[nm++] = (int32_t)u;
+                        }
+                    }
+                }
+            }
+            st_unique += nm;
+            ndL[v].len = 0;
+            for (int64_t k = 0; k < nm; ++k) {
+                const uint32_t u = (uint32_t)msgs[k];
+                const row_t* Lu = &L->rows[order[u]];
+                int pruned = 0;
+                for (int64_t i = 0; i < Lu->len; ++i) {
+                    ++st_checks;
+                    const int32_t tv = Tv[Lu->hub[i]];
+                    if (tv != INF_D && tv + (int32_t)Lu->dist[i] <= d) {
+                        pruned = 1;
+                        break;
+                    }
+                }
+                if (!pruned) row_push(&ndL[v], u, (uint8_t)(d > 255 ? 255 : d));
+            }
+            for (int64_t i = 0; i < Lv->len; ++i) Tv[Lv->hub[i]] = INF_D;
+            for (int64_t k = 0; k < nm; ++k) seen[msgs[k]] = -1;
+        }
+        for (int64_t v = 0; v < n; ++v) {                 /* L(v) <- L(v) U dL(v) */
+            row_t* nv = &ndL[v];
+            if (nv->len == 0) {
+                dL[v].len = 0;
+                continue;
+            }
+            if (d > 254) {
+                fail = 1;
+                break;
+            }
+            ++active;
+            st_acc += nv->len;
+            /* keep rows sorted by hub rank: insertion merge */
+            row_t* Lv = &L->rows[v];
+            for (int64_t k = 0; k < nv->len; ++k) {
+                if (row_push(Lv, nv->hub[k], (uint8_t)d)) fail = 1;
+                int64_t p = Lv->len - 1;
+                while (p > 0 && Lv->hub[p - 1] > Lv->hub[p]) {
+                    uint32_t th = Lv->hub[p]; Lv->hub[p] = Lv->hub[p - 1]; Lv->hub[p - 1] = th;
+                    uint8_t td = Lv->dist[p]; Lv->dist[p] = Lv->dist[p - 1]; Lv->dist[p - 1] = td;
+                    --p;
+                }
+            }
+            row_t t = dL[v];
+            dL[v] = *nv;
+            *nv = t;
+            nv->len = 0;
+        }
+        if (d < 256) {
+            L->stats[4 * d + 0] = st_msgs;
+            L->stats[4 * d + 1] = st_unique;
+            L->stats[4 * d + 2] = st_acc;
+            L->stats[4 * d + 3] = st_checks;
+        }
+    }
+    L->rounds = d;
+    for (int64_t v = 0; v < n; ++v) {
+        free(dL[v].hub); free(dL[v].dist);
+        free(ndL[v].hub); free(ndL[v].dist);
+    }
+    free(dL); free(ndL); free(rank); free(Tv); free(seen); free(msgs);
+    if (fail) {
+        oracle_labels_free(L);
+        return NULL;
+    }
+    finish_totals(L);
+    return L;
+}
+
+/* ----------------------------------------------------------------- Def. 2 */
+/* Canonical label of ONE vertex v: BFS from v; best[x] = smallest rank over
+ * all vertices on all shortest v-x paths (both ends included).  x is a hub of
+ * v iff best[x] == rank(x).  Writes (hub rank, distance) sorted by rank and
+ * returns the count (at most cap; -1 if cap is too small).  Scratch: dist and
+ * best must hold n entries and start as -1 / anything; dist is restored. */
+static int64_t chhl_row_impl(int64_t n, const int64_t* off, const int32_t* col, const int32_t* rank,
+                             int32_t v, int32_t* dist, int32_t* best, int32_t* Q,
+                             uint32_t* out_hub, uint8_t* out_dist, int64_t cap) {
+    (void)n;
+    int64_t head = 0, tail = 0;
+    Q[tail++] = v;
+    dist[v] = 0;
+    best[v] = rank[v];
+    while (head < tail) {
+        const int32_t p = Q[head++];
+        for (int64_t j = off[p]; j < off[p + 1]; ++j) {
+            const int32_t x = col[j];
+            if (dist[x] < 0) {
+                dist[x] = dist[p] + 1;
+                best[x] = rank[x] < best[p] ? rank[x] : best[p];
+                Q[tail++] = x;
+            } else if (dist[x] == dist[p] + 1 && best[p] < best[x]) {
+                best[x] = best[p];                       /* another shortest path into x */
+            }
+        }
+    }
+    int64_t k = 0;
+    for (int64_t i = 0; i < tail; ++i) {
+        const int32_t x = Q[i];
+        if (best[x] == rank[x]) {
+            if (k < cap) {
+                out_hub[k] = (uint32_t)rank[x];
+                out_dist[k] = (uint8_t)(dist[x] > 255 ? 255 : dist[x]);
+            }
+            ++k;
+        }
+    }
+    for (int64_t i = 0; i < tail; ++i) dist[Q[i]] = -1;
+    if (k > cap) return -1;
+    /* sort by hub rank (insertion sort; rows are short) */
+    for (int64_t i = 1; i < k; ++i) {
+        uint32_t h = out_hub[i];
+        uint8_t dd = out_dist[i];
+        int64_t p = i;
+        while (p > 0 && out_hub[p - 1] > h) {
+            out_hub[p] = out_hub[p - 1];
+            out_dist[p] = out_dist[p - 1];
+            --p;
+        }
+        out_hub[p] = h;
+        out_dist[p] = dd;
+    }
+    return k;
+}
+
+int64_t oracle_chhl_row(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order,
+                        int32_t v, uint32_t* out_hub, uint8_t* out_dist, int64_t cap) {
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* best = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * nn);
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t i = 0; i < n; ++i) dist[i] = -1;
+    int64_t k = chhl_row_impl(n, off, col, rank, v, dist, best, Q, out_hub, out_dist, cap);
+    free(rank); free(dist); free(best); free(Q);
+    return k;
+}
+
+/* Def. 2 for every vertex (n BFS runs; small graphs only). */
+void* oracle_chhl(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order) {
+    labels_t* L = labels_new(n);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* best = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * nn);
+    uint32_t* hh = (uint32_t*)malloc(sizeof(uint32_t) * nn);
+    uint8_t* dd = (uint8_t*)malloc(nn);
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t i = 0; i < n; ++i) dist[i] = -1;
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t k = chhl_row_impl(n, off, col, rank, (int32_t)v, dist, best, Q, hh, dd, n);
+        for (int64_t i = 0; i < k; ++i) row_push(&L->rows[v], hh[i], dd[i]);
+    }
+    free(rank); free(dist); free(best); free(Q); free(hh); free(dd);
+    finish_totals(L);
+    return L;
+}
+
+/* ------------------------------------------------------------ 2-hop query */
+/* labels as CSR (off, hub sorted per row, dist); pairs[2q]; out[q]. */
+void oracle_query(int64_t q, const int64_t* off, const uint32_t* hub, const uint8_t* dist,
+                  const int32_t* pairs, int32_t* out) {
+    for (int64_t k = 0; k < q; ++k) {
+        const int32_t s = pairs[2 * k], t = pairs[2 * k + 1];
+        int64_t i = off[s], ie = off[s + 1], j = off[t], je = off[t + 1];
+        int32_t best = -1;
+        while (i < ie && j < je) {
+            if (hub[i] < hub[j]) {
+                ++i;
+            } else if (hub[i] > hub[j]) {
+                ++j;
+            } else {
+                const int32_t c = (int32_t)dist[i] + (int32_t)dist[j];
+                if (best < 0 || c < best) best = c;
+                ++i;
+                ++j;
+            }
+        }
+        out[k] = best;
+    }
+}
+
+/* -------------------------------------------------------------------- BFS */
+void oracle_bfs(int64_t n, const int64_t* off, const int32_t* col, int32_t src, int32_t* dist) {
+    int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) dist[i] = -1;
+    int64_t head = 0, tail = 0;
+    Q[tail++] = src;
+    dist[src] = 0;
+    while (head < tail) {
+        const int32_t p = Q[head++];
+        for (int64_t j = off[p]; j < off[p + 1]; ++j)
+            if (dist[col[j]] < 0) {
+                dist[col[j]] = dist[p] + 1;
+                Q[tail++] = col[j];
+            }
+    }
+    free(Q);
+}
