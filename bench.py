@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Labeling throughput benchmark (edges/sec, % of HBM roofline) plus batched
+query throughput/latency, on a synthetic power-law graph.
+
+Default workload: Chung-Lu graph, 2^20 vertices, mean degree 16, exponent 2.1,
+seed 2, degree-descending order (ties by id).  One step = one plb_build of the
+whole graph (all rounds, from the rank-space relabel to the final by-id label
+layout) with the CSR already resident on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank labels its own replica of
+the graph (a single graph is not partitioned); value = edges of all ranks /
+max-over-ranks time ("replicas", weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Algorithmic bytes of the gather + prune kernels (all tiers), per unit counted
+# by the build itself:
+BYTES_PER_RECEIVER = 16 + 16 + 4 + 8  # CSR row bounds, label row bounds, list entry, new frontier descriptor
+BYTES_PER_ARC = 4 + 8                 # neighbour id, its frontier descriptor
+BYTES_PER_MESSAGE = 4                 # one frontier hub read
+BYTES_PER_STAGED = 4                  # one L(v) entry staged into the hub map
+BYTES_PER_CANDIDATE = 16              # label row bounds of the candidate hub
+BYTES_PER_PROBED = 4                  # one L(h) entry probed
+BYTES_PER_ACCEPTED = 4                # one new frontier hub written
+
+
+def gather_prune_bytes(st: dict, n: int) -> int:
+    return (BYTES_PER_RECEIVER * sum(st["receivers"]) + BYTES_PER_ARC * st["arcs_scanned"]
+            + BYTES_PER_MESSAGE * st["messages"] + BYTES_PER_STAGED * st["staged_entries"]
+            + BYTES_PER_CANDIDATE * st["unique_candidates"] + BYTES_PER_PROBED * st["probed_entries"]
+            + BYTES_PER_ACCEPTED * (st["total_labels"] - n))
+
+
+def measured_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                t = [x.strip() for x in line.split(",")]
+                if len(t) >= 9:
+                    rows.append(t)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_total_labels(name: str) -> int | None:
+    """Canonical label total of a named workload, as written by
+    oracle/workload_totals.py (a full oracle PLL run)."""
+    try:
+        with open(os.path.join(ROOT, "oracle", "workload_totals.json")) as f:
+            return int(json.load(f)[name]["labels"])
+    except Exception:
+        return None
+
+
+def pll_sample(g, order, total: int, seconds: float) -> dict:
+    """The oracle's sequential PLL (Alg. 1) on a bounded sample of this
+    workload: the first roots in rank order for about `seconds`, scaled to the
+    whole graph by the share of all labels produced (the total comes from a
+    full oracle run).  Early roots produce labels fastest, so this estimate
+    favours the CPU."""
+    import oracle as O
+
+    lab, roots, el = O.pll_budget(g.off, g.col, order, seconds)
+    frac = lab.total / max(total, 1)
+    est = el / max(frac, 1e-12)
+    return {"value": g.m / est, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": (f"PLL (Alg. 1) over the first {roots} roots in rank order ({el:.1f} s, "
+                       f"{lab.total} of {total} labels = {100 * frac:.1f}%); time scaled by label share"),
+            "sample_seconds": el}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on this workload (rank 0 only)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1906_12018_gb300 import graphs as G
+
+    g = G.workload(args.workload)
+    order = G.degree_order(g)
+    total = oracle_total_labels(args.workload)
+    if total is None:
+        import oracle as O
+
+        total = O.pll(g.off, g.col, order).total
+    samples = []
+    for step in range(args.warmup + args.steps):
+        s = pll_sample(g, order, total, args.ref_seconds)
+        if step >= args.warmup:
+            samples.append(s)
+    v = statistics.median(s["value"] for s in samples)
+    sec = statistics.median(s["sample_seconds"] for s in samples)
+    line = {"metric": "labeling edges/sec", "value": v, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * sec, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": g.n, "m": g.m}, "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "edges/s",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chunglu20")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_1906_12018_gb300 import graphs as G
+    from paper_1906_12018_gb300 import plb
+
+    world, rank, local = dist_init()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    g = G.workload(args.workload)
+    order = G.degree_order(g)
+    rp = torch.from_numpy(g.off).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    o = torch.from_numpy(order).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = plb.default_options()
+
+    for _ in range(max(args.warmup, 3)):
+        lab = plb.build(rp, col, o, opts)
+        lab.free()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    labs = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    with ClockSampler(local if world > 1 else 0) as clk:
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between steps (outside the events)
+            ev[k][0].record(stream)
+            labs.append(plb.build(rp, col, o, opts))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = max_over_ranks(ms, world)
+    st0 = labs[0].stats()
+    n_labels = labs[0].total
+    launches = st0["launches"] * args.steps
+    for lab in labs:
+        lab.free()
+    labs = []
+
+    # kernel-class timings and counters: one profiled build
+    lab = plb.build(rp, col, o, default_options_profile())
+    st = lab.stats()
+    gp_ms = sum(st["ms_gather_prune"])
+    gp_bytes = gather_prune_bytes(st, g.n)
+    peak, peak_kind = measured_peaks()
+    achieved = gp_bytes / (gp_ms / 1e3) / 1e9 if gp_ms > 0 else 0.0
+
+    # batched queries on the resident labels: 65,536 uniform pairs per launch
+    qpairs = torch.from_numpy(G.uniform_pairs(g.n, 1 << 16, 4)).to(dev)
+    out = torch.empty(1 << 16, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        lab.query(qpairs, out)
+    qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for a, b in qev:
+        flush.zero_()
+        a.record(stream)
+        lab.query(qpairs, out)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    qms = sorted(a.elapsed_time(b) for a, b in qev)
+    q_value = (1 << 16) / (statistics.median(qms) / 1e3)
+    lab.free()
+
+    # end to end through the public API: pinned host CSR -> device, build,
+    # labels -> pinned host
+    h_rp = torch.from_numpy(g.off).pin_memory()
+    h_col = torch.from_numpy(g.col).pin_memory()
+    h_o = torch.from_numpy(order).pin_memory()
+    h2d = h_rp.numel() * 8 + h_col.numel() * 4 + h_o.numel() * 4
+    d2h = 0
+    e2e_ms = []
+    for k in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        d_rp = h_rp.to(dev, non_blocking=True)
+        d_col = h_col.to(dev, non_blocking=True)
+        d_o = h_o.to(dev, non_blocking=True)
+        lab = plb.build(d_rp, d_col, d_o, opts)
+        off_d, hub_d, dist_d = lab.device_arrays()
+        h_off = torch.empty(off_d.shape, dtype=off_d.dtype, pin_memory=True)
+        h_hub = torch.empty(hub_d.shape, dtype=hub_d.dtype, pin_memory=True)
+        h_dist = torch.empty(dist_d.shape, dtype=dist_d.dtype, pin_memory=True)
+        h_off.copy_(off_d, non_blocking=True)
+        h_hub.copy_(hub_d, non_blocking=True)
+        h_dist.copy_(dist_d, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+        d2h = h_off.numel() * 8 + h_hub.numel() * 4 + h_dist.numel()
+        lab.free()
+    e2e_ms_med = max_over_ranks(statistics.median(e2e_ms), world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        total = oracle_total_labels(args.workload)
+        if total is not None:
+            cpu = pll_sample(g, order, total, args.cpu_seconds)
+
+    if rank == 0:
+        value = g.m * world / (ms_max / 1e3)
+        line = {
+            "metric": "labeling edges/sec",
+            "value": value,
+            "unit": "edges/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": max(args.warmup, 3),
+            "ms_per_step": ms_max,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": g.n, "m": g.m, "labels": n_labels,
+                       "rounds": st0["rounds"], "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": "gather+prune (k_gp_warp/k_gp_block/k_gp_global)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
+                         "traffic": None, "algorithmic_bytes": gp_bytes, "kernel_ms": gp_ms,
+                         "build_ms_profiled": st["ms_total"]},
+            "kernel_ms": {"prepare": st["ms_prepare"], "frontier": st["ms_frontier"],
+                          "gather_prune": st["ms_gather_prune"], "merge": st["ms_merge"],
+                          "finalize": st["ms_finalize"]},
+            "e2e": {"value": g.m * world / (e2e_ms_med / 1e3), "unit": "edges/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_med},
+            "queries": {"value": q_value, "unit": "queries/s", "batch": 1 << 16,
+                        "p50_ms": qms[len(qms) // 2], "p99_ms": qms[min(len(qms) - 1, int(0.99 * len(qms)))]},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "wall_s_timed": wall,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def default_options_profile():
+    from paper_1906_12018_gb300 import plb
+
+    return plb.default_options(profile=1)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

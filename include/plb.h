@@ -1,0 +1,186 @@
+/*
+ * plb.h -- C ABI of the GB300 (sm_103a) canonical 2-hop distance labeling
+ * library ("pruned landmark labeling" built round by round, vertex-centric).
+ *
+ * Method: Jin, Peng, Wu, Dragan, Agrawal, Ren, "Pruned Landmark Labeling
+ * Meets Vertex Centric Computation" (arXiv 1906.12018).
+ *   - labels: Def. 2 (canonical hierarchical hub labeling, Sec. 2.1): for a
+ *     total order pi, h is a hub of v iff h has the highest rank on every
+ *     shortest h-v path; the label entry stores d(h, v).
+ *   - construction: Alg. 3 (VC-PLL, Sec. 3.1), one vertex-centric round per
+ *     distance d = 1, 2, ...; Thm. 1 shows it yields the labels of Def. 2.
+ *   - query: Sec. 2.1, Dis(u,v) = min over common hubs h of d(u,h)+d(h,v).
+ *
+ * General conventions
+ *   - Every pointer argument that names graph, order, pair or distance data
+ *     is a DEVICE pointer (CUDA global memory of the current device) unless
+ *     its comment says "host".  Inputs are read-only for the duration of the
+ *     call and stay owned by the caller.
+ *   - Calls are ordered on the given stream (NULL = the legacy default
+ *     stream).  plb_build / plb_build_batch synchronise the stream internally
+ *     (one device->host read per round); plb_query_batch and
+ *     plb_degree_order are asynchronous: results are ready when the stream is.
+ *   - Vertices are int32 ids 0..n-1.  "rank" r in 0..n-1 is the position in
+ *     the vertex order (rank 0 = highest); order[r] = id of rank r.
+ *   - Limits: n < 2^24 (16,777,216 vertices; a label entry packs a 24-bit hub
+ *     rank with an 8-bit distance), label distances <= 254.
+ *   - Every entry point returns an int status (PLB_OK = 0) and never throws.
+ *     On an error, no output object is created and nothing is returned
+ *     through out-parameters.
+ */
+#ifndef PLB_H
+#define PLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* plb_stream; /* == cudaStream_t */
+
+/* ---------------------------------------------------------------- status */
+enum plb_status {
+    PLB_OK = 0,
+    PLB_ERR_INVALID = 1,        /* bad argument, bad CSR, order not a permutation */
+    PLB_ERR_OOM = 2,            /* device allocation failed */
+    PLB_ERR_DIST_OVERFLOW = 3,  /* a label distance would exceed 254 */
+    PLB_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired */
+    PLB_ERR_CUDA = 5,           /* a CUDA runtime call or launch failed */
+    PLB_ERR_TOO_LARGE = 6       /* n >= 2^24 */
+};
+
+#define PLB_MAX_VERTICES (1 << 24)
+#define PLB_MAX_DIST 254
+#define PLB_UNREACHABLE (-1) /* query answer: s and t are in different components */
+#define PLB_BAD_PAIR (-2)    /* query answer: s or t outside [0, n) */
+
+/* Undirected unweighted graph as a symmetric CSR (device memory).
+ * row_ptr[n+1] (row_ptr[0] = 0, row_ptr[n] = nnz, non-decreasing);
+ * col[nnz] neighbour ids, each row strictly ascending (no duplicates), no
+ * self-loops, and (u,v) present iff (v,u) present.  nnz = 2 * edges. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+} plb_csr;
+
+/* Build options; plb_default_options fills the defaults. */
+typedef struct {
+    int32_t validate;          /* 1: check CSR and order on the device first (default 1) */
+    int32_t warp_label_cap;    /* largest |L(v)| handled one-vertex-per-warp (default 512) */
+    int32_t warp_cand_cap;     /* largest unique-candidate count per warp-vertex (default 256) */
+    int32_t block_label_cap;   /* largest |L(v)| handled one-vertex-per-block in shared memory */
+    int32_t block_cand_cap;    /* largest candidate count for the block tier */
+    int32_t block_threads;     /* threads of the block tier (multiple of 32, <= 1024) */
+    int32_t use_graph;         /* 1: run the round loop as a captured CUDA graph with a
+                                  device-side while condition (no per-round host sync) */
+    int32_t profile;           /* 1: time each kernel class with CUDA events */
+    int32_t reserved[8];
+} plb_options;
+
+/* Opaque label set (library-owned device memory; free with plb_labels_free). */
+typedef struct plb_labels plb_labels;
+
+/* Borrowed view of a label set: valid until plb_labels_free.
+ * Rows indexed by ORIGINAL vertex id; entries of a row sorted by hub rank
+ * ascending; hub = rank of the hub vertex; dist = d(hub, v) (0 for v itself). */
+typedef struct {
+    int64_t n;
+    int64_t total;            /* sum of |L(v)| */
+    const int64_t* off;       /* device, n+1 */
+    const uint32_t* hub;      /* device, total */
+    const uint8_t* dist;      /* device, total */
+    const int32_t* order;     /* device, n: rank -> id used by the build */
+    int32_t max_dist;         /* largest stored distance */
+    int32_t rounds;           /* vertex-centric rounds executed (the last accepts nothing) */
+} plb_label_view;
+
+/* Counters and timings of one build (Sec. 3.3 / 4.3 cost terms). */
+#define PLB_MAX_ROUNDS 256
+typedef struct {
+    int32_t rounds;
+    int32_t reruns;                 /* rounds repeated after growing a scratch buffer */
+    int64_t n, nnz, total_labels;
+    /* per round d (index d, 1..rounds) */
+    int64_t receivers[PLB_MAX_ROUNDS];   /* vertices that gathered messages */
+    int64_t accepted[PLB_MAX_ROUNDS];    /* new labels (|dL_d|) */
+    /* totals over rounds */
+    int64_t arcs_scanned;           /* neighbour entries read in the gather */
+    int64_t messages;               /* dL entries read by the gather (before dedup, before rank filter) */
+    int64_t unique_candidates;      /* distinct (h, v) pairs checked */
+    int64_t staged_entries;         /* L(v) entries staged into the hub map */
+    int64_t probed_entries;         /* L(h) entries probed in distance checks */
+    int64_t tier_vertices[3];       /* vertex-rounds handled by warp / block / global tier */
+    /* milliseconds on the device (profile = 1 only; else 0) */
+    double ms_total, ms_prepare, ms_frontier, ms_gather_prune[3], ms_merge, ms_finalize;
+    int64_t launches;               /* kernels launched by this build */
+} plb_build_stats;
+
+/* Fill *opt with defaults. */
+void plb_default_options(plb_options* opt);
+
+/* Build the canonical labels (Def. 2) of g under vertex_order (device,
+ * int32[n], rank -> id, a permutation of [0,n)) by vertex-centric rounds
+ * (Alg. 3).  On success *out receives a new label set.
+ * Errors: PLB_ERR_INVALID (null pointers, n < 0, nnz < 0, a CSR or order that
+ * breaks the rules above -- checked on the device when opt->validate),
+ * PLB_ERR_TOO_LARGE, PLB_ERR_OOM, PLB_ERR_DIST_OVERFLOW, PLB_ERR_CUDA. */
+int plb_build(const plb_csr* g, const int32_t* vertex_order, const plb_options* opt,
+              plb_stream stream, plb_labels** out);
+
+/* Build k independent graphs in ONE round loop over their disjoint union
+ * (host arrays gs[k], orders[k] of device pointers; outs[k] host array that
+ * receives k label sets).  By Def. 2 a disjoint union's canonical labels,
+ * under any order that keeps each part's own order, are the parts' labels,
+ * so each outs[i] equals plb_build(&gs[i], orders[i]).  The union of the
+ * parts must have fewer than 2^24 vertices.  Errors as plb_build; on error
+ * no label set is returned. */
+int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k,
+                    const plb_options* opt, plb_stream stream, plb_labels** outs);
+
+/* Answer q distance queries (Sec. 2.1): pairs (device, int32[2q],
+ * s_i = pairs[2i], t_i = pairs[2i+1], original ids) -> dist_out (device,
+ * int32[q]): d(s,t), PLB_UNREACHABLE if no common hub, PLB_BAD_PAIR if an id
+ * is outside [0,n).  Asynchronous on the stream; returns PLB_ERR_INVALID for
+ * null pointers or q < 0. */
+int plb_query_batch(const plb_labels* labels, const int32_t* pairs, int64_t q,
+                    int32_t* dist_out, plb_stream stream);
+
+/* Same query over several label sets in one launch: pair i is answered on
+ * sets[set_idx[i]] (set_idx device int32[q]); sets is a host array of m label
+ * sets that must all stay alive until the stream reaches this work.  A pair
+ * whose set index is outside [0,m) gets PLB_BAD_PAIR. */
+int plb_query_multi(const plb_labels* const* sets, int64_t m, const int32_t* set_idx,
+                    const int32_t* pairs, int64_t q, int32_t* dist_out, plb_stream stream);
+
+/* Borrow device pointers of a label set. */
+int plb_labels_view(const plb_labels* labels, plb_label_view* view);
+
+/* Counters/timings of the build that produced the label set. */
+int plb_labels_stats(const plb_labels* labels, plb_build_stats* stats);
+
+/* Device bytes held by a label set. */
+int64_t plb_labels_bytes(const plb_labels* labels);
+
+/* Release a label set (synchronises the device first). NULL is accepted. */
+int plb_labels_free(plb_labels* labels);
+
+/* Degree order (Sec. 6.1: vertices ordered by degree): order_out (device,
+ * int32[n]) receives rank -> id, degree descending, ties by smaller id.
+ * Only row_ptr is read.  Allocates device scratch (8 bytes per vertex,
+ * rounded up to a power of two).  Asynchronous on the stream. */
+int plb_degree_order(const plb_csr* g, int32_t* order_out, plb_stream stream);
+
+/* Human-readable status text (static storage). */
+const char* plb_strerror(int status);
+
+/* ABI version: 100 * major + minor. */
+int plb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLB_H */

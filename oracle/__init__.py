@@ -59,6 +59,8 @@ def _load():
         f = getattr(lib, name)
         f.argtypes = [I64, P, P, P]
         f.restype = P
+    lib.oracle_pll_budget.argtypes = [I64, P, P, P, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+    lib.oracle_pll_budget.restype = P
     lib.oracle_chhl_row.argtypes = [I64, P, P, P, ctypes.c_int32, P, P, I64]
     lib.oracle_chhl_row.restype = I64
     lib.oracle_labels_free.argtypes = [P]
@@ -146,6 +148,22 @@ def _run(fname, off, col, order) -> Labels:
 def pll(off, col, order) -> Labels:
     """Alg. 1 (PLL with the small revision)."""
     return _run("oracle_pll", off, col, order)
+
+
+def pll_budget(off, col, order, seconds: float):
+    """Alg. 1 over the roots in rank order, stopped once ``seconds`` have
+    elapsed (checked between roots).  Returns (labels so far, roots done,
+    elapsed seconds); a bounded sample for timing the oracle."""
+    import time
+
+    n, off, col, order = _csr_args(off, col, order)
+    done = ctypes.c_int64(0)
+    t0 = time.perf_counter()
+    h = _load().oracle_pll_budget(n, _p(off), _p(col), _p(order), float(seconds), ctypes.byref(done))
+    el = time.perf_counter() - t0
+    if not h:
+        raise OverflowError("label distance above 254 (or out of memory)")
+    return _export(h, n), int(done.value), el
 
 
 def vcpll(off, col, order) -> Labels:

@@ -33,6 +33,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 typedef struct {
     uint32_t* hub;
@@ -118,8 +119,19 @@ static void finish_totals(labels_t* L) {
 #define INF_D 0x7fffffff
 
 /* ----------------------------------------------------------------- Alg. 1 */
-/* Returns NULL on allocation failure or when a label distance exceeds 254. */
-void* oracle_pll(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order) {
+static double now_s(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* Returns NULL on allocation failure or when a label distance exceeds 254.
+ * With budget_s > 0 the roots loop stops after the first root that ends past
+ * the budget (a bounded sample for timing); *roots_done receives the number
+ * of roots processed. */
+static void* pll_impl(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order,
+                      double budget_s, int64_t* roots_done) {
+    const double t_start = now_s();
     labels_t* L = labels_new(n);
     int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     int32_t* T = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));  /* hub rank -> d(u,hub) */
@@ -131,7 +143,9 @@ void* oracle_pll(int64_t n, const int64_t* off, const int32_t* col, const int32_
         T[i] = INF_D;
         D[i] = -1;
     }
-    for (int64_t r = 0; r < n && !fail; ++r) {           /* roots from high to low rank */
+    int64_t r = 0;
+    for (r = 0; r < n && !fail; ++r) {                   /* roots from high to low rank */
+        if (budget_s > 0 && r > 0 && now_s() - t_start > budget_s) break;
         const int32_t u = order[r];
         const row_t* Lu = &L->rows[u];
         const int64_t lu_len = Lu->len;                  /* L(u) before this root */
@@ -176,12 +190,23 @@ void* oracle_pll(int64_t n, const int64_t* off, const int32_t* col, const int32_
     free(T);
     free(D);
     free(Q);
+    if (roots_done) *roots_done = r;
     if (fail) {
         oracle_labels_free(L);
         return NULL;
     }
     finish_totals(L);
     return L;
+}
+
+void* oracle_pll(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order) {
+    return pll_impl(n, off, col, order, 0.0, NULL);
+}
+
+/* Alg. 1 stopped after budget_s seconds (between roots); labels so far. */
+void* oracle_pll_budget(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order,
+                        double budget_s, int64_t* roots_done) {
+    return pll_impl(n, off, col, order, budget_s, roots_done);
 }
 
 /* ----------------------------------------------------------------- Alg. 3 */

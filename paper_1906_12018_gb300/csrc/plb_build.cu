@@ -1,0 +1,439 @@
+// Host driver of the labeling build: validation, rank-space relabel, the
+// round loop of Alg. 3 (Sec. 3.1) and the final by-id label layout.
+#include <algorithm>
+#include <cstddef>
+#include <cstring>
+#include <vector>
+
+#include "plb_round.cuh"
+
+namespace plb {
+
+namespace {
+
+constexpr int kFlatThreads = 256;
+constexpr int kGpWarpThreads = 256;
+
+struct DevPool {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    bool failed = false;
+    explicit DevPool(cudaStream_t st) : s(st) {}
+    template <typename T>
+    T* alloc(int64_t count) {
+        void* p = nullptr;
+        const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+            (void)cudaGetLastError();
+            failed = true;
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    void release(void* p) {
+        auto it = std::find(ptrs.begin(), ptrs.end(), p);
+        if (it != ptrs.end()) {
+            cudaFreeAsync(p, s);
+            ptrs.erase(it);
+        }
+    }
+    ~DevPool() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+};
+
+struct Timer {
+    bool on;
+    cudaStream_t s;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
+    explicit Timer(bool enabled, cudaStream_t st) : on(enabled), s(st) {}
+    cudaEvent_t mark() {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        return e;
+    }
+    void span(int cls, cudaEvent_t a, cudaEvent_t b) { ev[cls].push_back({a, b}); }
+    double total(int cls) {
+        double t = 0;
+        for (auto& p : ev[cls]) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, p.first, p.second);
+            t += ms;
+        }
+        return t;
+    }
+    ~Timer() {
+        for (auto& v : ev)
+            for (auto& p : v) {
+                cudaEventDestroy(p.first);
+                cudaEventDestroy(p.second);
+            }
+    }
+};
+enum { T_PREP = 0, T_FRONT = 1, T_GPW = 2, T_GPB = 3, T_GPG = 4, T_MERGE = 5, T_FINAL = 6, T_ALL = 7 };
+
+int grid_for(int64_t items, int threads, int max_blocks) {
+    int64_t b = (items + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (int)b;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 132;
+    }
+    return sms;
+}
+
+int pow2_at_least(int64_t x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+// Core build on a validated-or-trusted CSR.  Returns a status; on success
+// *out holds the labels (rows by original id).
+int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
+               const plb_options& o, cudaStream_t s, plb_labels** out) {
+#define PLB_CK(x)                                   \
+    do {                                            \
+        if ((x) != cudaSuccess) {                   \
+            (void)cudaGetLastError();               \
+            return PLB_ERR_CUDA;                    \
+        }                                           \
+    } while (0)
+#define PLB_ALLOC_OK() \
+    do {               \
+        if (pool.failed) return PLB_ERR_OOM; \
+    } while (0)
+
+    DevPool pool(s);
+    Timer tm(o.profile != 0, s);
+    plb_build_stats st{};
+    st.n = n;
+    st.nnz = nnz;
+    const int sms = num_sms();
+    const int flat_grid_cap = sms * 8;
+    cudaEvent_t t_all0 = tm.on ? tm.mark() : nullptr;
+
+    RoundCounters* ctr = pool.alloc<RoundCounters>(1);
+    int* err = pool.alloc<int>(4);
+    PLB_ALLOC_OK();
+    RoundCounters* hctr = nullptr;
+    PLB_CK(cudaMallocHost(&hctr, sizeof(RoundCounters)));
+    struct HostFree {
+        void* p;
+        ~HostFree() { cudaFreeHost(p); }
+    } hf{hctr};
+    PLB_CK(cudaMemsetAsync(ctr, 0, sizeof(RoundCounters), s));
+    PLB_CK(cudaMemsetAsync(err, 0, 4 * sizeof(int), s));
+
+    cudaEvent_t t0 = tm.on ? tm.mark() : nullptr;
+    // ---------------------------------------------------------- validation
+    if (o.validate) {
+        k_check_rowptr<<<grid_for(n + 1, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(row_ptr, n, nnz, err);
+        PLB_CK(cudaGetLastError());
+        int herr = 0;
+        PLB_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PLB_CK(cudaStreamSynchronize(s));
+        st.launches += 1;
+        if (herr) return PLB_ERR_INVALID;
+        int* seen = pool.alloc<int>(n);
+        PLB_ALLOC_OK();
+        PLB_CK(cudaMemsetAsync(seen, 0, sizeof(int) * std::max<int64_t>(n, 1), s));
+        if (nnz > 0) {
+            k_check_cols<<<grid_for((nnz + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(row_ptr, col, n,
+                                                                                               nnz, err);
+            PLB_CK(cudaGetLastError());
+        }
+        k_check_order<<<grid_for(n, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(order, n, seen, err);
+        PLB_CK(cudaGetLastError());
+        PLB_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PLB_CK(cudaStreamSynchronize(s));
+        st.launches += 2;
+        pool.release(seen);
+        if (herr) return PLB_ERR_INVALID;
+    }
+
+    // ---------------------------------------------------- rank-space CSR
+    int32_t* inv = pool.alloc<int32_t>(n);
+    int64_t* roff = pool.alloc<int64_t>(n + 1);
+    int32_t* rcol = pool.alloc<int32_t>(nnz);
+    int64_t* tmp64 = pool.alloc<int64_t>(n + 1);
+    int64_t* scan_scr = pool.alloc<int64_t>(scan_scratch_elems(n + 1));
+    PLB_ALLOC_OK();
+    const int gflat = grid_for(n, kFlatThreads, flat_grid_cap);
+    k_inverse<<<gflat, kFlatThreads, 0, s>>>(order, inv, n);
+    k_rank_degree<<<gflat, kFlatThreads, 0, s>>>(row_ptr, order, tmp64, n);
+    PLB_CK(cudaGetLastError());
+    PLB_CK(exclusive_scan_i64(tmp64, roff, n, scan_scr, s));
+    if (nnz > 0) {
+        k_relabel<<<grid_for((nnz + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(row_ptr, col, order, inv,
+                                                                                          roff, rcol, n, nnz);
+        PLB_CK(cudaGetLastError());
+    }
+    st.launches += 4;
+
+    // ------------------------------------------------------------ state
+    int64_t lcap[2] = {std::max<int64_t>(2 * n, 1024), std::max<int64_t>(2 * n, 1024)};
+    int64_t* loff[2] = {pool.alloc<int64_t>(n + 1), pool.alloc<int64_t>(n + 1)};
+    uint32_t* lent[2] = {pool.alloc<uint32_t>(lcap[0]), pool.alloc<uint32_t>(lcap[1])};
+    int64_t fcap[2] = {std::max<int64_t>(nnz / 2 + n, 1024), std::max<int64_t>(nnz / 2 + n, 1024)};
+    uint64_t* fse[2] = {pool.alloc<uint64_t>(n), pool.alloc<uint64_t>(n)};
+    uint32_t* fhub[2] = {pool.alloc<uint32_t>(fcap[0]), pool.alloc<uint32_t>(fcap[1])};
+    uint8_t* recv = pool.alloc<uint8_t>(n);
+    int32_t* A = pool.alloc<int32_t>(n);
+    int32_t* R = pool.alloc<int32_t>(n);
+    int32_t* O1 = pool.alloc<int32_t>(n);
+    int32_t* O2 = pool.alloc<int32_t>(n);
+    int64_t* aoff = pool.alloc<int64_t>(n + 1);
+    PLB_ALLOC_OK();
+    PLB_CK(cudaMemsetAsync(recv, 0, std::max<int64_t>(n, 1), s));
+    k_init<<<gflat, kFlatThreads, 0, s>>>(roff, n, loff[0], lent[0], fse[0], fhub[0], A, ctr);
+    PLB_CK(cudaGetLastError());
+    st.launches += 1;
+    int64_t T = n;  // labels so far
+    int cur = 0;    // index of current L and previous frontier
+    if (tm.on) tm.span(T_PREP, t0, tm.mark());
+
+    // tier geometry
+    const int warp_cand = pow2_at_least(std::max(32, o.warp_cand_cap));
+    const int warp_label = std::max(16, o.warp_label_cap);
+    const int w_log_s = ceil_log2_i64(2 * warp_cand);
+    const int w_log_m = ceil_log2_i64(2 * warp_label);
+    const int warps_per_block = kGpWarpThreads / 32;
+    const size_t w_smem = sizeof(uint32_t) * (4 * warps_per_block +
+                                              (size_t)warps_per_block * ((1 << w_log_s) + (1 << w_log_m) + warp_cand));
+    const int bthr = std::min(1024, std::max(64, (o.block_threads / 32) * 32));
+    const int block_cand = pow2_at_least(std::max(bthr, o.block_cand_cap));
+    const int b_log_s = ceil_log2_i64(2 * (int64_t)block_cand);
+    const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);
+    const size_t b_smem = sizeof(uint32_t) * (16 + (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) + block_cand);
+    if (w_smem > 227 * 1024 || b_smem > 227 * 1024) return PLB_ERR_INVALID;
+    PLB_CK(cudaFuncSetAttribute(k_gp_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w_smem));
+    PLB_CK(cudaFuncSetAttribute(k_gp_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_smem));
+    int occ_w = 1, occ_b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_gp_warp, kGpWarpThreads, w_smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_gp_block, bthr, b_smem);
+    const int grid_w = sms * std::max(1, occ_w);
+    const int grid_b = sms * std::max(1, occ_b);
+    uint32_t* gscratch = nullptr;
+    int64_t gwords = 0;
+    const int g_blocks = 16;
+
+    // ------------------------------------------------------------ rounds
+    int status = PLB_OK;
+    int d = 0;
+    for (;;) {
+        ++d;
+        const int nxt = cur ^ 1;
+        cudaEvent_t r0 = tm.on ? tm.mark() : nullptr;
+        // frontier: mark receivers from the active list, collect them
+        k_active_degree<<<gflat, kFlatThreads, 0, s>>>(roff, A, ctr, tmp64, n);
+        PLB_CK(exclusive_scan_i64(tmp64, aoff, n, scan_scr, s));
+        k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[cur], fhub[cur], A, aoff, ctr, recv, n);
+        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse[nxt], R, O1, ctr, warp_label,
+                                                 (int64_t)32 * 64);
+        k_after_collect<<<1, 1, 0, s>>>(ctr);
+        PLB_CK(cudaGetLastError());
+        st.launches += 5;
+        cudaEvent_t r1 = tm.on ? tm.mark() : nullptr;
+        if (tm.on) tm.span(T_FRONT, r0, r1);
+        bool rerun = false;
+        for (;;) {
+            GpParams p{};
+            p.roff = roff;
+            p.rcol = rcol;
+            p.loff = loff[cur];
+            p.lent = lent[cur];
+            p.fse = fse[cur];
+            p.fhub = fhub[cur];
+            p.fse_new = fse[nxt];
+            p.fhub_new = fhub[nxt];
+            p.fcap = (unsigned long long)fcap[nxt];
+            p.ctr = ctr;
+            p.d = (uint32_t)d;
+            if (rerun) {
+                k_rerun_reset<<<gflat, kFlatThreads, 0, s>>>(ctr, fse[nxt], n);
+                st.launches += 1;
+            }
+            cudaEvent_t g0 = tm.on ? tm.mark() : nullptr;
+            // warp tier
+            p.list = R;
+            p.list_n = &ctr->nR;
+            p.esc = O1;
+            p.esc_n = &ctr->nO1;
+            p.log_s = w_log_s;
+            p.log_m = w_log_m;
+            p.cand_limit = warp_cand;
+            p.label_limit = warp_label;
+            k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
+            cudaEvent_t g1 = tm.on ? tm.mark() : nullptr;
+            // block tier
+            p.list = O1;
+            p.list_n = &ctr->nO1;
+            p.esc = O2;
+            p.esc_n = &ctr->nO2;
+            p.log_s = b_log_s;
+            p.log_m = b_log_m;
+            p.cand_limit = block_cand;
+            k_gp_block<<<grid_b, bthr, b_smem, s>>>(p);
+            cudaEvent_t g2 = tm.on ? tm.mark() : nullptr;
+            PLB_CK(cudaGetLastError());
+            st.launches += 2;
+            if (tm.on) {
+                tm.span(T_GPW, g0, g1);
+                tm.span(T_GPB, g1, g2);
+            }
+            PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+            PLB_CK(cudaStreamSynchronize(s));
+            if (hctr->nO2 > 0) {
+                // global tier: tables in global scratch, sized for any vertex
+                if (!gscratch) {
+                    const int64_t big = (int64_t)pow2_at_least(2 * n + 2 * bthr);
+                    gwords = 2 * big + pow2_at_least(n + 1);
+                    gscratch = pool.alloc<uint32_t>(gwords * g_blocks);
+                    PLB_ALLOC_OK();
+                }
+                p.list = O2;
+                p.list_n = &ctr->nO2;
+                p.esc = O2;
+                p.esc_n = &ctr->nO2;
+                p.gscratch = gscratch;
+                p.gscratch_words = gwords;
+                cudaEvent_t q0 = tm.on ? tm.mark() : nullptr;
+                k_gp_global<<<g_blocks, bthr, 0, s>>>(p);
+                cudaEvent_t q1 = tm.on ? tm.mark() : nullptr;
+                PLB_CK(cudaGetLastError());
+                st.launches += 1;
+                if (tm.on) tm.span(T_GPG, q0, q1);
+                PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+                PLB_CK(cudaStreamSynchronize(s));
+            }
+            if (!hctr->fovf) break;
+            // new-frontier buffer too small: grow it and run the gather again
+            const int64_t need = (int64_t)hctr->cursor;
+            pool.release(fhub[nxt]);
+            fcap[nxt] = need + need / 2 + 1024;
+            fhub[nxt] = pool.alloc<uint32_t>(fcap[nxt]);
+            PLB_ALLOC_OK();
+            st.reruns += 1;
+            rerun = true;
+        }
+        const int64_t acc = (int64_t)hctr->accepted;
+        if (d < PLB_MAX_ROUNDS) {
+            st.receivers[d] = (int64_t)hctr->nR + hctr->nO1_base;
+            st.accepted[d] = acc;
+        }
+        st.arcs_scanned += (int64_t)hctr->arcs;
+        st.messages += (int64_t)hctr->msgs;
+        st.unique_candidates += (int64_t)hctr->uniq;
+        st.staged_entries += (int64_t)hctr->staged;
+        st.probed_entries += (int64_t)hctr->probed;
+        for (int k = 0; k < 3; ++k) st.tier_vertices[k] += (int64_t)hctr->tier[k];
+        if (acc == 0) break;
+        if (d > PLB_MAX_DIST) {
+            status = PLB_ERR_DIST_OVERFLOW;
+            break;
+        }
+        // merge: L <- L U dL_d (rows stay sorted by hub rank)
+        cudaEvent_t m0 = tm.on ? tm.mark() : nullptr;
+        const int64_t Tn = T + acc;
+        if (Tn > lcap[nxt]) {
+            pool.release(lent[nxt]);
+            lcap[nxt] = Tn + Tn / 4 + 1024;
+            lent[nxt] = pool.alloc<uint32_t>(lcap[nxt]);
+            PLB_ALLOC_OK();
+        }
+        k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[cur], fse[nxt], n, tmp64, A, ctr);
+        PLB_CK(exclusive_scan_i64(tmp64, loff[nxt], n, scan_scr, s));
+        k_merge_old<<<grid_for((T + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(
+            loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], n);
+        k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
+            loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], A, ctr, (uint32_t)d);
+        PLB_CK(cudaGetLastError());
+        st.launches += 5;
+        if (tm.on) tm.span(T_MERGE, m0, tm.mark());
+        T = Tn;
+        cur = nxt;
+        // round-start reset of the per-round counters (nA carries over)
+        PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
+        PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 2, s));
+        // grow the frontier buffer ahead of a large round
+        if (acc > fcap[cur ^ 1] / 2) {
+            const int nx2 = cur ^ 1;
+            pool.release(fhub[nx2]);
+            fcap[nx2] = 2 * acc + 1024;
+            fhub[nx2] = pool.alloc<uint32_t>(fcap[nx2]);
+            PLB_ALLOC_OK();
+        }
+    }
+    st.rounds = d;
+    st.total_labels = T;
+    if (status != PLB_OK) return status;
+
+    // ------------------------------------------------------------ finalize
+    cudaEvent_t f0 = tm.on ? tm.mark() : nullptr;
+    plb_labels* L = new plb_labels();
+    L->n = n;
+    L->total = T;
+    L->rounds = d;
+    auto fail = [&](int code) {
+        if (L->off) cudaFreeAsync(L->off, s);
+        if (L->packed) cudaFreeAsync(L->packed, s);
+        if (L->hub) cudaFreeAsync(L->hub, s);
+        if (L->dist) cudaFreeAsync(L->dist, s);
+        if (L->order) cudaFreeAsync(L->order, s);
+        delete L;
+        return code;
+    };
+    if (cudaMallocAsync((void**)&L->off, sizeof(int64_t) * (n + 1), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&L->packed, sizeof(uint32_t) * std::max<int64_t>(T, 1), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&L->hub, sizeof(uint32_t) * std::max<int64_t>(T, 1), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&L->dist, std::max<int64_t>(T, 1), s) != cudaSuccess ||
+        cudaMallocAsync((void**)&L->order, sizeof(int32_t) * std::max<int64_t>(n, 1), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(PLB_ERR_OOM);
+    }
+    L->bytes = (int64_t)(sizeof(int64_t) * (n + 1) + 9 * (size_t)T + 4 * (size_t)n);
+    k_final_len<<<gflat, kFlatThreads, 0, s>>>(loff[cur], inv, n, tmp64);
+    if (exclusive_scan_i64(tmp64, L->off, n, scan_scr, s) != cudaSuccess) return fail(PLB_ERR_CUDA);
+    k_finalize<<<grid_for((T + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(
+        loff[cur], lent[cur], inv, L->off, L->packed, L->hub, L->dist, n, ctr);
+    if (cudaMemcpyAsync(L->order, order, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(PLB_ERR_CUDA);
+    if (cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return fail(PLB_ERR_CUDA);
+    st.launches += 4;
+    cudaEvent_t f1 = tm.on ? tm.mark() : nullptr;
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(PLB_ERR_CUDA);
+    L->max_dist = (int32_t)hctr->max_dist;
+    if (tm.on) {
+        tm.span(T_FINAL, f0, f1);
+        tm.span(T_ALL, t_all0, f1);
+        st.ms_prepare = tm.total(T_PREP);
+        st.ms_frontier = tm.total(T_FRONT);
+        st.ms_gather_prune[0] = tm.total(T_GPW);
+        st.ms_gather_prune[1] = tm.total(T_GPB);
+        st.ms_gather_prune[2] = tm.total(T_GPG);
+        st.ms_merge = tm.total(T_MERGE);
+        st.ms_finalize = tm.total(T_FINAL);
+        st.ms_total = tm.total(T_ALL);
+    }
+    L->stats = st;
+    *out = L;
+    return PLB_OK;
+#undef PLB_CK
+#undef PLB_ALLOC_OK
+}
+
+}  // namespace plb

@@ -1,0 +1,64 @@
+// Kernels of the vertex-centric labeling rounds (Alg. 3, Sec. 3.1), in rank
+// space: vertex i is the vertex of rank i, so "h outranks v" is h < v.
+//
+// Per round d (labels L and frontier dL_{d-1} as they stood after round d-1):
+//   k_mark         every active a (dL_{d-1}(a) non-empty) flags the neighbours
+//                  v that some hub of dL_{d-1}(a) outranks (scatter, Alg. 3).
+//   k_collect      flagged vertices become this round's receivers; heavy ones
+//                  (large |L(v)| or degree) go straight to the block tier.
+//   k_gp_warp      gather + dedup + distance check, one vertex per warp, with
+//                  L(v) staged hub-keyed in shared memory (the gather of
+//                  Alg. 3: unique messages, then d < min over common hubs).
+//   k_gp_block     the same with one vertex per block (bigger tables).
+//   k_gp_global    the same with tables in global scratch (any size).
+//   k_merge_*      L(v) <- L(v) U dL_d(v), keeping rows sorted by hub rank.
+#pragma once
+
+#include "plb_internal.cuh"
+
+namespace plb {
+
+struct RoundCounters {
+    unsigned long long cursor;    // append cursor of the new frontier buffer
+    unsigned long long accepted;  // new labels this round
+    unsigned long long arcs, msgs, uniq, staged, probed;
+    unsigned long long tier[3];
+    int nR, nO1, nO2, nA;         // receivers (warp tier), block tier, global tier, next active
+    int nO1_base;                 // block-tier entries made by k_collect (for reruns)
+    int fovf;                     // new-frontier buffer overflow
+    unsigned int max_dist;        // finalize: largest stored distance
+    int pad;
+    unsigned long long active_arcs;  // arcs of the active list (mark work)
+};
+
+struct GpParams {
+    const int64_t* roff;
+    const int32_t* rcol;
+    const int64_t* loff;
+    const uint32_t* lent;
+    const uint64_t* fse;       // frontier of round d-1: start|count per vertex
+    const uint32_t* fhub;      // frontier hubs of round d-1 (rows sorted)
+    uint64_t* fse_new;         // frontier of round d
+    uint32_t* fhub_new;
+    unsigned long long fcap;   // capacity of fhub_new
+    const int32_t* list;       // vertices handled by this tier
+    const int* list_n;
+    int32_t* esc;              // escalation list (next tier)
+    int* esc_n;
+    RoundCounters* ctr;
+    uint32_t d;                // round = distance of accepted labels
+    int log_s, log_m;          // warp/block tier table sizes (log2 slots)
+    int cand_limit;            // max unique candidates (power of two)
+    int label_limit;           // max |L(v)| (block tier: escalate beyond)
+    uint32_t* gscratch;        // global tier: per-block table storage
+    int64_t gscratch_words;    // words per block
+};
+
+struct WarpSync {
+    __device__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
+
+}  // namespace plb

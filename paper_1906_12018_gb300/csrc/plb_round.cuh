@@ -1,0 +1,41 @@
+// Declarations of the round kernels (defined in plb_round.cu).
+#pragma once
+
+#include "plb_kernels.cuh"
+
+namespace plb {
+
+__global__ void k_check_rowptr(const int64_t* row_ptr, int64_t n, int64_t nnz, int* err);
+__global__ void k_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int* err);
+__global__ void k_check_order(const int32_t* order, int64_t n, int* seen, int* err);
+__global__ void k_inverse(const int32_t* order, int32_t* inv, int64_t n);
+__global__ void k_rank_degree(const int64_t* row_ptr, const int32_t* order, int64_t* rdeg, int64_t n);
+__global__ void k_relabel(const int64_t* row_ptr, const int32_t* col, const int32_t* order, const int32_t* inv,
+                          const int64_t* roff, int32_t* rcol, int64_t n, int64_t nnz);
+__global__ void k_init(const int64_t* roff, int64_t n, int64_t* loff, uint32_t* lent, uint64_t* fse,
+                       uint32_t* fhub, int32_t* A, RoundCounters* ctr);
+__global__ void k_active_degree(const int64_t* roff, const int32_t* A, const RoundCounters* ctr, int64_t* adeg,
+                                int64_t n);
+__global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t* fse, const uint32_t* fhub,
+                       const int32_t* A, const int64_t* aoff, const RoundCounters* ctr, uint8_t* recv, int64_t n);
+__global__ void k_collect(uint8_t* recv, const int64_t* roff, const int64_t* loff, int64_t n, uint64_t* fse_new,
+                          int32_t* R, int32_t* O1, RoundCounters* ctr, int64_t warp_label_limit,
+                          int64_t warp_deg_limit);
+__global__ void k_after_collect(RoundCounters* ctr);
+__global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n);
+__global__ void k_gp_warp(GpParams p);
+__global__ void k_gp_block(GpParams p);
+__global__ void k_gp_global(GpParams p);
+__global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int64_t n, int64_t* newlen, int32_t* A,
+                              RoundCounters* ctr);
+__global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
+                            const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n);
+__global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
+                            const uint64_t* fse_new, const uint32_t* fhub_new, const int32_t* A,
+                            const RoundCounters* ctr, uint32_t d);
+__global__ void k_final_len(const int64_t* loff, const int32_t* inv, int64_t n, int64_t* len);
+__global__ void k_finalize(const int64_t* loff, const uint32_t* lent, const int32_t* inv, const int64_t* out_off,
+                           uint32_t* out_packed, uint32_t* out_hub, uint8_t* out_dist, int64_t n,
+                           RoundCounters* ctr);
+
+}  // namespace plb

@@ -1,0 +1,69 @@
+"""C-ABI library checks that need no GPU: it builds, loads, and exports every
+entry point that include/plb.h declares (no compute calls are made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "plb.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(plb_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1906_12018_gb300 import build_ext
+
+    if not os.path.exists(build_ext.LIB):
+        build_ext.build()
+    return ctypes.CDLL(build_ext.LIB)
+
+
+def test_header_declares_the_boundary():
+    fns = declared_functions()
+    for name in ("plb_build", "plb_query_batch", "plb_labels_view", "plb_labels_free", "plb_build_batch",
+                 "plb_degree_order", "plb_strerror"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_symbol():
+    from paper_1906_12018_gb300 import plb
+
+    assert sorted(plb.exported_symbols()) == declared_functions()
+
+
+def test_host_only_entry_points(lib):
+    from paper_1906_12018_gb300 import plb
+
+    lib = plb._lib()
+    assert lib.plb_version() == 100
+    assert lib.plb_strerror(0) == b"ok"
+    assert b"254" in lib.plb_strerror(3)
+    o = plb.default_options()
+    assert o.validate == 1 and o.warp_label_cap > 0 and o.block_threads % 32 == 0
+    # argument errors are reported before any device work
+    h = ctypes.c_void_p()
+    assert lib.plb_build(None, None, None, None, ctypes.byref(h)) == plb.PLB_ERR_INVALID
+    g = plb.CSR(1 << 24, 0, 1, None)
+    assert lib.plb_build(ctypes.byref(g), 1, None, None, ctypes.byref(h)) == plb.PLB_ERR_TOO_LARGE
+    assert lib.plb_query_batch(None, None, 1, None, None) == plb.PLB_ERR_INVALID
+    assert lib.plb_labels_free(None) == 0
+
+
+def test_struct_layouts_match_header():
+    from paper_1906_12018_gb300 import plb
+
+    assert ctypes.sizeof(plb.Options) == 16 * 4
+    assert ctypes.sizeof(plb.CSR) == 32
+    assert ctypes.sizeof(plb.LabelView) == 6 * 8 + 8

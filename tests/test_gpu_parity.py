@@ -1,0 +1,242 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Labels must be bit-exact as hub-sorted rows (hub rank, distance); query
+answers must be bit-exact (integers, no tolerance).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1906_12018_gb300 import graphs as G
+from paper_1906_12018_gb300 import plb
+
+from gpu_util import assert_labels_equal, gpu_build, gpu_query, host_labels, to_device
+from test_oracle import apsp, tiny_graphs
+
+pytestmark = pytest.mark.gpu
+
+
+def orders_for(g, seed=3):
+    rng = np.random.default_rng(seed)
+    return [G.degree_order(g), np.arange(g.n, dtype=np.int32), rng.permutation(g.n).astype(np.int32)]
+
+
+@pytest.mark.parametrize("name,g", tiny_graphs(), ids=lambda x: x if isinstance(x, str) else "")
+def test_tiny_graphs_match_definition(name, g):
+    for order in orders_for(g):
+        ref = O.chhl(g.off, g.col, order)
+        lab = gpu_build(g, order)
+        assert_labels_equal(lab, ref, name)
+
+
+@pytest.fixture(scope="module")
+def rmat12():
+    g = G.workload("rmat12")
+    order = G.degree_order(g)
+    return g, order, O.pll(g.off, g.col, order)
+
+
+def test_rmat12_labels_bit_exact(rmat12):
+    g, order, ref = rmat12
+    lab = gpu_build(g, order)
+    assert_labels_equal(lab, ref, "rmat12")
+    assert lab.max_dist == ref.max_dist
+
+
+def test_rmat12_queries_bit_exact(rmat12):
+    g, order, ref = rmat12
+    lab = gpu_build(g, order)
+    pairs = G.uniform_pairs(g.n, 10_000, 1)
+    got = gpu_query(lab, pairs)
+    assert np.array_equal(got, O.query(ref, pairs))
+    D = apsp(g)
+    want = D[pairs[:, 0], pairs[:, 1]]
+    assert np.array_equal(got, np.where(np.isfinite(want), want, -1).astype(np.int64))
+
+
+def test_rmat12_rounds_match_vcpll(rmat12):
+    """Per round: the same number of new labels as Alg. 3 restated on the CPU,
+    and the same number of distinct checked candidates."""
+    g, order, _ = rmat12
+    vc = O.vcpll(g.off, g.col, order)
+    lab = gpu_build(g, order)
+    st = lab.stats()
+    assert st["rounds"] == vc.rounds
+    assert st["accepted"] == [int(x) for x in vc.round_stats[1:vc.rounds + 1, 2]]
+    assert st["unique_candidates"] == int(vc.round_stats[:, 1].sum())
+
+
+def test_all_tiers_bit_exact(rmat12):
+    """Tiny table capacities push vertices through the block and the global
+    tier; the labels must not change."""
+    g, order, ref = rmat12
+    lab = gpu_build(g, order, warp_cand_cap=32, warp_label_cap=16, block_cand_cap=64, block_label_cap=24,
+                    block_threads=64)
+    assert_labels_equal(lab, ref, "forced tiers")
+    st = lab.stats()
+    assert all(t > 0 for t in st["tier_vertices"]), st["tier_vertices"]
+
+
+def test_edge_cases():
+    # no vertices
+    g0 = G.from_edges(0, [])
+    lab = gpu_build(g0, np.zeros(0, np.int32))
+    assert lab.total == 0 and lab.n == 0
+    # single vertex, isolated vertices
+    for n in (1, 7):
+        g = G.from_edges(n, [])
+        order = G.degree_order(g)
+        lab = gpu_build(g, order)
+        assert_labels_equal(lab, O.pll(g.off, g.col, order), f"isolated{n}")
+        assert np.array_equal(gpu_query(lab, [[0, n - 1], [0, 0]]), [0 if n == 1 else -1, 0])
+    # star, complete graph, path reaching the largest distance 254
+    cases = [G.from_edges(40, [(0, i) for i in range(1, 40)]),
+             G.from_edges(25, [(i, j) for i in range(25) for j in range(i + 1, 25)]),
+             G.from_edges(255, [(i, i + 1) for i in range(254)])]
+    for g in cases:
+        order = G.degree_order(g)
+        lab = gpu_build(g, order)
+        assert_labels_equal(lab, O.pll(g.off, g.col, order))
+    assert lab.max_dist == 254
+
+
+def test_distance_overflow_is_an_error():
+    g = G.from_edges(300, [(i, i + 1) for i in range(299)])
+    with pytest.raises(plb.PLBError) as e:
+        gpu_build(g, np.arange(300, dtype=np.int32))
+    assert e.value.code == plb.PLB_ERR_DIST_OVERFLOW
+
+
+def _bad_build(off, col, order):
+    dev = torch.device("cuda:0")
+    rp = torch.tensor(off, dtype=torch.int64, device=dev)
+    c = torch.tensor(col, dtype=torch.int32, device=dev)
+    o = torch.tensor(order, dtype=torch.int32, device=dev)
+    with pytest.raises(plb.PLBError) as e:
+        plb.build(rp, c, o)
+    return e.value.code
+
+
+def test_invalid_inputs_rejected():
+    ok_off, ok_col = [0, 1, 3, 4], [1, 0, 2, 1]           # path 0-1-2
+    assert _bad_build([0, 1, 3, 4], [1, 0, 2, 0], [0, 1, 2]) == plb.PLB_ERR_INVALID   # asymmetric
+    assert _bad_build([0, 1, 3, 4], [1, 2, 0, 1], [0, 1, 2]) == plb.PLB_ERR_INVALID   # unsorted row
+    assert _bad_build([0, 2, 4, 5], [0, 1, 0, 2, 1], [0, 1, 2]) == plb.PLB_ERR_INVALID  # self-loop
+    assert _bad_build([0, 1, 3, 4], [1, 0, 7, 1], [0, 1, 2]) == plb.PLB_ERR_INVALID   # out of range
+    assert _bad_build([0, 1, 4, 5], [1, 0, 2, 2, 1], [0, 1, 2]) == plb.PLB_ERR_INVALID  # duplicate
+    assert _bad_build([0, 3, 3, 4], ok_col, [0, 1, 2]) == plb.PLB_ERR_INVALID        # bad row_ptr
+    assert _bad_build(ok_off, ok_col, [0, 1, 1]) == plb.PLB_ERR_INVALID               # order not a permutation
+    assert _bad_build(ok_off, ok_col, [0, 1, 5]) == plb.PLB_ERR_INVALID               # order out of range
+
+
+def test_degree_order_matches_generator(rmat12):
+    for g in (rmat12[0], G.small_graph(1), G.from_edges(5, [(0, 1)])):
+        rp, _, _ = to_device(g, np.zeros(g.n, np.int32))
+        got = plb.degree_order(rp)
+        torch.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy(), G.degree_order(g))
+
+
+def test_batch_equals_single_and_oracle():
+    gs = [G.small_graph(i) for i in range(10)] + [G.from_edges(3, [(0, 1)]), G.workload("rmat12")]
+    orders = [G.degree_order(g) for g in gs]
+    dev = [to_device(g, o) for g, o in zip(gs, orders)]
+    batch = plb.build_batch(dev)
+    for i, (g, o) in enumerate(zip(gs, orders)):
+        single = plb.build(*dev[i])
+        a = host_labels(batch[i])
+        b = host_labels(single)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y), i
+        if g.n <= 40_000:
+            ref = O.pll(g.off, g.col, o)
+            assert_labels_equal(batch[i], ref, f"batch part {i}")
+        pairs = G.uniform_pairs(g.n, 500, 7 + i)
+        assert np.array_equal(gpu_query(batch[i], pairs), gpu_query(single, pairs))
+
+
+def test_query_multi_matches_single(rmat12):
+    g1, o1, _ = rmat12
+    g2 = G.small_graph(3)
+    o2 = G.degree_order(g2)
+    l1 = gpu_build(g1, o1)
+    l2 = gpu_build(g2, o2)
+    rng = np.random.default_rng(5)
+    q = 4000
+    sidx = rng.integers(0, 2, q).astype(np.int32)
+    sidx[:3] = [5, -1, 2]  # bad set indices
+    n = np.where(sidx == 1, g2.n, g1.n)
+    pairs = (rng.random((q, 2)) * n[:, None]).astype(np.int32)
+    got = plb.query_multi([l1, l2], torch.from_numpy(sidx).cuda(), torch.from_numpy(pairs).cuda())
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    assert np.all(got[:3] == plb.PLB_BAD_PAIR)
+    for k, lab in ((0, l1), (1, l2)):
+        m = sidx == k
+        assert np.array_equal(got[m], gpu_query(lab, pairs[m]))
+    bad = gpu_query(l1, [[0, g1.n], [-1, 0]])
+    assert np.all(bad == plb.PLB_BAD_PAIR)
+
+
+@pytest.fixture(scope="module")
+def chunglu20():
+    g = G.workload("chunglu20")
+    order = G.degree_order(g)
+    lab = gpu_build(g, order)
+    return g, order, lab
+
+
+def test_chunglu20_sampled_rows_match_definition(chunglu20):
+    """Full-size bench graph, default launch configuration: 64 sampled rows
+    equal Def. 2 computed one vertex at a time."""
+    g, order, lab = chunglu20
+    off, hub, dist = host_labels(lab)
+    rng = np.random.default_rng(20)
+    deg = g.degrees()
+    picks = list(rng.choice(g.n, 48, replace=False)) + list(order[:8]) + list(np.argsort(-deg)[100:108])
+    for v in picks:
+        h, d = O.chhl_row(g.off, g.col, order, int(v))
+        a, b = int(off[v]), int(off[v + 1])
+        assert np.array_equal(hub[a:b], h), v
+        assert np.array_equal(dist[a:b], d), v
+
+
+def test_chunglu20_sampled_queries_match_bfs(chunglu20):
+    g, order, lab = chunglu20
+    rng = np.random.default_rng(21)
+    srcs = rng.choice(g.n, 12, replace=False)
+    pairs = []
+    for s in srcs:
+        t = rng.choice(g.n, 500, replace=False)
+        pairs.append(np.stack([np.full(500, s), t], 1))
+    pairs = np.concatenate(pairs).astype(np.int32)
+    got = gpu_query(lab, pairs)
+    for i, s in enumerate(srcs):
+        D = O.bfs(g.off, g.col, int(s))
+        assert np.array_equal(got[i * 500:(i + 1) * 500], D[pairs[i * 500:(i + 1) * 500, 1]])
+
+
+def test_chunglu20_invariants(chunglu20):
+    g, order, lab = chunglu20
+    off, hub, dist = host_labels(lab)
+    rank = np.empty(g.n, dtype=np.int64)
+    rank[order] = np.arange(g.n)
+    lens = np.diff(off)
+    last = off[1:] - 1
+    assert np.all(lens >= 1)
+    assert np.array_equal(hub[last].astype(np.int64), rank)           # (v, 0) closes every row
+    assert np.all(dist[last] == 0)
+    row = np.repeat(np.arange(g.n), lens)
+    assert np.all(hub.astype(np.int64) <= rank[row])                  # hierarchy
+    inner = np.ones(hub.shape[0], bool)
+    inner[off[:-1]] = False
+    assert np.all(np.diff(hub.astype(np.int64))[inner[1:]] > 0)       # strictly increasing rows
+
+
+@pytest.mark.slow
+def test_chunglu20_full_oracle(chunglu20):
+    """Every label of the 2^20-vertex graph against the sequential PLL oracle."""
+    g, order, lab = chunglu20
+    ref = O.pll(g.off, g.col, order)
+    assert_labels_equal(lab, ref, "chunglu20")
