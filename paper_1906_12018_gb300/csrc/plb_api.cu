@@ -152,6 +152,7 @@ int plb_build(const plb_csr* g, const int32_t* vertex_order, const plb_options* 
     if (opt) o = *opt; else plb_default_options(&o);
     if (!sane_options(o)) return PLB_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
     if (g->n == 0) return empty_labels(out, s);
     return plb::build_core(g->row_ptr, g->col, vertex_order, g->n, g->nnz, o, s, out);
 }
@@ -165,6 +166,7 @@ int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k, 
     if (opt) o = *opt; else plb_default_options(&o);
     if (!sane_options(o)) return PLB_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
     std::vector<plb::GraphDesc> hd((size_t)k);
     std::vector<int64_t> vb((size_t)k + 1), eb((size_t)k + 1);
     int64_t N = 0, E = 0;

@@ -47,11 +47,13 @@ struct Timer {
     bool on;
     cudaStream_t s;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
+    std::vector<cudaEvent_t> all;  // every event once (spans may share an end point)
     explicit Timer(bool enabled, cudaStream_t st) : on(enabled), s(st) {}
     cudaEvent_t mark() {
         cudaEvent_t e;
         cudaEventCreate(&e);
         cudaEventRecord(e, s);
+        all.push_back(e);
         return e;
     }
     void span(int cls, cudaEvent_t a, cudaEvent_t b) { ev[cls].push_back({a, b}); }
@@ -65,11 +67,8 @@ struct Timer {
         return t;
     }
     ~Timer() {
-        for (auto& v : ev)
-            for (auto& p : v) {
-                cudaEventDestroy(p.first);
-                cudaEventDestroy(p.second);
-            }
+        for (cudaEvent_t e : all) cudaEventDestroy(e);
+        (void)cudaGetLastError();
     }
 };
 enum { T_PREP = 0, T_FRONT = 1, T_GPW = 2, T_GPB = 3, T_GPG = 4, T_MERGE = 5, T_FINAL = 6, T_ALL = 7 };

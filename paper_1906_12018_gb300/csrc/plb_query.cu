@@ -102,6 +102,7 @@ extern "C" int plb_query_batch(const plb_labels* L, const int32_t* pairs, int64_
                                plb_stream stream) {
     if (!L || q < 0 || (q > 0 && (!pairs || !dist_out))) return PLB_ERR_INVALID;
     if (q == 0) return PLB_OK;
+    (void)cudaGetLastError();
     plb::k_query<<<plb::query_grid(q), plb::kQThreads, 0, (cudaStream_t)stream>>>(L->off, L->packed, L->n, pairs, q,
                                                                                   dist_out);
     return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
@@ -113,6 +114,7 @@ extern "C" int plb_query_multi(const plb_labels* const* sets, int64_t m, const i
     for (int64_t k = 0; k < m; ++k)
         if (!sets[k]) return PLB_ERR_INVALID;
     if (q == 0) return PLB_OK;
+    (void)cudaGetLastError();
     const int grid = plb::query_grid(q);
     for (int64_t lo = 0; lo < std::max<int64_t>(m, 1); lo += plb::kMaxSets) {
         plb::SetTable tab{};

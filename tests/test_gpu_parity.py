@@ -98,7 +98,11 @@ def test_edge_cases():
         order = G.degree_order(g)
         lab = gpu_build(g, order)
         assert_labels_equal(lab, O.pll(g.off, g.col, order))
-    assert lab.max_dist == 254
+    # path in position order: vertex i has every j <= i as a hub, up to d = 254
+    order = np.arange(255, dtype=np.int32)
+    lab = gpu_build(cases[-1], order)
+    assert_labels_equal(lab, O.pll(cases[-1].off, cases[-1].col, order))
+    assert lab.max_dist == 254 and lab.rounds == 255
 
 
 def test_distance_overflow_is_an_error():
