@@ -189,14 +189,14 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int64_t fcap[2] = {std::max<int64_t>(nnz / 2 + n, 1024), std::max<int64_t>(nnz / 2 + n, 1024)};
     uint64_t* fse[2] = {pool.alloc<uint64_t>(n), pool.alloc<uint64_t>(n)};
     uint32_t* fhub[2] = {pool.alloc<uint32_t>(fcap[0]), pool.alloc<uint32_t>(fcap[1])};
-    uint8_t* recv = pool.alloc<uint8_t>(n);
+    unsigned long long* recv = pool.alloc<unsigned long long>(n);
     int32_t* A = pool.alloc<int32_t>(n);
     int32_t* R = pool.alloc<int32_t>(n);
     int32_t* O1 = pool.alloc<int32_t>(n);
     int32_t* O2 = pool.alloc<int32_t>(n);
     int64_t* aoff = pool.alloc<int64_t>(n + 1);
     PLB_ALLOC_OK();
-    PLB_CK(cudaMemsetAsync(recv, 0, std::max<int64_t>(n, 1), s));
+    PLB_CK(cudaMemsetAsync(recv, 0, sizeof(unsigned long long) * std::max<int64_t>(n, 1), s));
     k_init<<<gflat, kFlatThreads, 0, s>>>(roff, n, loff[0], lent[0], fse[0], fhub[0], A, ctr);
     PLB_CK(cudaGetLastError());
     st.launches += 1;
@@ -212,11 +212,17 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     const int warps_per_block = kGpWarpThreads / 32;
     const size_t w_smem = sizeof(uint32_t) * (4 * warps_per_block +
                                               (size_t)warps_per_block * ((1 << w_log_s) + (1 << w_log_m) + warp_cand));
-    const int bthr = std::min(1024, std::max(64, (o.block_threads / 32) * 32));
+    const int bthr = std::min(512, std::max(64, (o.block_threads / 32) * 32));
     const int block_cand = pow2_at_least(std::max(bthr, o.block_cand_cap));
     const int b_log_s = ceil_log2_i64(2 * (int64_t)block_cand);
     const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);
-    const size_t b_smem = sizeof(uint32_t) * (16 + (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) + block_cand);
+    const size_t b_smem = sizeof(uint32_t) * (48 + (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) + block_cand);
+    TierLimits lim;
+    lim.warp_bound = 2 * (int64_t)warp_cand;
+    lim.warp_label = warp_label;
+    lim.warp_deg = (int64_t)32 * 64;
+    lim.block_cand = block_cand;
+    lim.block_label = ((int64_t(1) << b_log_m) - 2 * bthr) / 2;
     if (w_smem > 227 * 1024 || b_smem > 227 * 1024) return PLB_ERR_INVALID;
     PLB_CK(cudaFuncSetAttribute(k_gp_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w_smem));
     PLB_CK(cudaFuncSetAttribute(k_gp_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_smem));
@@ -240,11 +246,23 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         k_active_degree<<<gflat, kFlatThreads, 0, s>>>(roff, A, ctr, tmp64, n);
         PLB_CK(exclusive_scan_i64(tmp64, aoff, n, scan_scr, s));
         k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[cur], fhub[cur], A, aoff, ctr, recv, n);
-        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse[nxt], R, O1, ctr, warp_label,
-                                                 (int64_t)32 * 64);
+        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse[nxt], R, O1, O2, ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(ctr);
         PLB_CK(cudaGetLastError());
         st.launches += 5;
+        // size the new frontier buffer from the candidate bound (no re-run)
+        PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+        PLB_CK(cudaStreamSynchronize(s));
+        if ((int64_t)hctr->bound_sum > fcap[nxt]) {
+            const int64_t want = std::min<int64_t>((int64_t)hctr->bound_sum + 1024,
+                                                   std::max<int64_t>(int64_t(1) << 31, 2 * fcap[nxt]));
+            if (want > fcap[nxt]) {
+                pool.release(fhub[nxt]);
+                fcap[nxt] = want;
+                fhub[nxt] = pool.alloc<uint32_t>(fcap[nxt]);
+                PLB_ALLOC_OK();
+            }
+        }
         cudaEvent_t r1 = tm.on ? tm.mark() : nullptr;
         if (tm.on) tm.span(T_FRONT, r0, r1);
         bool rerun = false;
@@ -296,6 +314,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));
             if (hctr->nO2 > 0) {
+                cudaEvent_t q0 = tm.on ? tm.mark() : nullptr;
                 // global tier: tables in global scratch, sized for any vertex
                 if (!gscratch) {
                     const int64_t big = (int64_t)pow2_at_least(2 * n + 2 * bthr);
@@ -309,7 +328,6 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                 p.esc_n = &ctr->nO2;
                 p.gscratch = gscratch;
                 p.gscratch_words = gwords;
-                cudaEvent_t q0 = tm.on ? tm.mark() : nullptr;
                 k_gp_global<<<g_blocks, bthr, 0, s>>>(p);
                 cudaEvent_t q1 = tm.on ? tm.mark() : nullptr;
                 PLB_CK(cudaGetLastError());
@@ -330,7 +348,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
         const int64_t acc = (int64_t)hctr->accepted;
         if (d < PLB_MAX_ROUNDS) {
-            st.receivers[d] = (int64_t)hctr->nR + hctr->nO1_base;
+            st.receivers[d] = (int64_t)hctr->nR + hctr->nO1_base + hctr->nO2_base;
             st.accepted[d] = acc;
         }
         st.arcs_scanned += (int64_t)hctr->arcs;
@@ -366,7 +384,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         cur = nxt;
         // round-start reset of the per-round counters (nA carries over)
         PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
-        PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 2, s));
+        PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
         // grow the frontier buffer ahead of a large round
         if (acc > fcap[cur ^ 1] / 2) {
             const int nx2 = cur ^ 1;

@@ -23,12 +23,12 @@ struct RoundCounters {
     unsigned long long accepted;  // new labels this round
     unsigned long long arcs, msgs, uniq, staged, probed;
     unsigned long long tier[3];
-    int nR, nO1, nO2, nA;         // receivers (warp tier), block tier, global tier, next active
-    int nO1_base;                 // block-tier entries made by k_collect (for reruns)
+    unsigned long long bound_sum; // sum over receivers of the candidate bound min(v, messages)
+    int nR, nO1, nO2;             // receivers: warp tier, block tier, global tier
+    int nA;                       // next active list (kept across the per-round reset)
+    int nO1_base, nO2_base;       // tier-list sizes made by k_collect (for reruns)
     int fovf;                     // new-frontier buffer overflow
     unsigned int max_dist;        // finalize: largest stored distance
-    int pad;
-    unsigned long long active_arcs;  // arcs of the active list (mark work)
 };
 
 struct GpParams {
@@ -52,6 +52,15 @@ struct GpParams {
     int label_limit;           // max |L(v)| (block tier: escalate beyond)
     uint32_t* gscratch;        // global tier: per-block table storage
     int64_t gscratch_words;    // words per block
+};
+
+// Routing limits of k_collect (see the tier geometry in build_core).
+struct TierLimits {
+    int64_t warp_bound;   // candidate bound up to which the warp tier is tried
+    int64_t warp_label;   // largest |L(v)| of the warp tier
+    int64_t warp_deg;     // largest degree of the warp tier
+    int64_t block_cand;   // candidate bound up to which the block tier is used
+    int64_t block_label;  // largest |L(v)| of the block tier
 };
 
 struct WarpSync {

@@ -142,9 +142,12 @@ __global__ void k_active_degree(const int64_t* roff, const int32_t* A, const Rou
     }
 }
 
-// Flat over the arcs of the active list: flag v in N(a) if min dL(a) < v.
+// Flat over the arcs of the active list: v in N(a) receives when min dL(a) < v
+// (some new hub of a outranks v); recv[v] accumulates |dL(a)| over such
+// neighbours, an upper bound on v's messages.
 __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t* fse, const uint32_t* fhub,
-                       const int32_t* A, const int64_t* aoff, const RoundCounters* ctr, uint8_t* recv, int64_t n) {
+                       const int32_t* A, const int64_t* aoff, const RoundCounters* ctr, unsigned long long* recv,
+                       int64_t n) {
     __shared__ int64_t sh_r[2];
     const int64_t nA = ctr->nA;
     if (nA == 0) return;
@@ -159,50 +162,58 @@ __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t*
         for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
             const int64_t i = row_of(aoff, r0, r1, p);
             const int32_t a = A[i];
-            const uint32_t minh = fhub[fstart(fse[a])];
+            const uint64_t f = fse[a];
+            const uint32_t minh = fhub[fstart(f)];
             const int32_t v = rcol[roff[a] + (p - aoff[i])];
-            if ((uint32_t)v > minh) recv[v] = 1;
+            if ((uint32_t)v > minh) atomicAdd(recv + v, (unsigned long long)fcount(f));
         }
     }
 }
 
-// Receivers: flagged vertices.  Vertices with |L(v)| > warp_label_limit or
-// degree > warp_deg_limit go to the block tier directly.  Also clears the
-// flags and the new frontier descriptors.
-__global__ void k_collect(uint8_t* recv, const int64_t* roff, const int64_t* loff, int64_t n, uint64_t* fse_new,
-                          int32_t* R, int32_t* O1, RoundCounters* ctr, int64_t warp_label_limit,
-                          int64_t warp_deg_limit) {
+// Receivers (recv[v] > 0) are routed by the candidate bound min(v, recv[v]),
+// |L(v)| and degree: warp tier (R), block tier (O1) or global tier (O2).
+// Also clears recv and the new frontier descriptors, and sums the bounds.
+__global__ void k_collect(unsigned long long* recv, const int64_t* roff, const int64_t* loff, int64_t n,
+                          uint64_t* fse_new, int32_t* R, int32_t* O1, int32_t* O2, RoundCounters* ctr,
+                          TierLimits lim) {
+    unsigned long long bsum = 0;
+    const int lane = lane_id();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         fse_new[v] = 0;
-        const bool r = recv[v] != 0;
-        bool heavy = false;
-        if (r) {
+        const unsigned long long c = recv[v];
+        int tier = -1;
+        if (c) {
             recv[v] = 0;
-            heavy = (loff[v + 1] - loff[v]) > warp_label_limit || (roff[v + 1] - roff[v]) > warp_deg_limit;
+            const unsigned long long bound = c < (unsigned long long)v ? c : (unsigned long long)v;
+            bsum += bound;
+            const int64_t ll = loff[v + 1] - loff[v];
+            const int64_t deg = roff[v + 1] - roff[v];
+            if ((int64_t)bound <= lim.warp_bound && ll <= lim.warp_label && deg <= lim.warp_deg) tier = 0;
+            else if ((int64_t)bound <= lim.block_cand && ll <= lim.block_label) tier = 1;
+            else tier = 2;
         }
         const unsigned am = __activemask();
-        const unsigned mw = __ballot_sync(am, r && !heavy);
-        const unsigned mh = __ballot_sync(am, r && heavy);
-        const int lane = lane_id();
-        if (mw) {
-            const int leader = __ffs(mw) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&ctr->nR, __popc(mw));
-            base = __shfl_sync(am, base, leader);
-            if (r && !heavy) R[base + __popc(mw & ((1u << lane) - 1u))] = (int32_t)v;
-        }
-        if (mh) {
-            const int leader = __ffs(mh) - 1;
-            int base = 0;
-            if (lane == leader) base = atomicAdd(&ctr->nO1, __popc(mh));
-            base = __shfl_sync(am, base, leader);
-            if (r && heavy) O1[base + __popc(mh & ((1u << lane) - 1u))] = (int32_t)v;
+        int32_t* lists[3] = {R, O1, O2};
+        int* counts[3] = {&ctr->nR, &ctr->nO1, &ctr->nO2};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const unsigned m = __ballot_sync(am, tier == t);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(counts[t], __popc(m));
+                base = __shfl_sync(am, base, leader);
+                if (tier == t) lists[t][base + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+            }
         }
     }
+    bsum = warp_sum(bsum);
+    if (lane == 0 && bsum) atomicAdd(&ctr->bound_sum, bsum);
 }
 
 __global__ void k_after_collect(RoundCounters* ctr) {
     ctr->nO1_base = ctr->nO1;
+    ctr->nO2_base = ctr->nO2;
     ctr->nA = 0;
 }
 
@@ -212,7 +223,7 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
         fse_new[v] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->nO1 = ctr->nO1_base;
-        ctr->nO2 = 0;
+        ctr->nO2 = ctr->nO2_base;
         ctr->cursor = 0;
         ctr->accepted = 0;
         ctr->fovf = 0;
@@ -222,211 +233,57 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
 }
 
 // ------------------------------------------------------- gather + prune
-// One warp per vertex v:
-//  1. stage L(v) into the hub-keyed map M (shared memory);
-//  2. gather: for every neighbour a and every h in dL_{d-1}(a) with h < v and
-//     h not already a hub of v, insert h into the set S (unique messages);
-//  3. check each h in S: accept iff no w in L(h) has M[w] + d(w,h) <= d
-//     (the distance check of Alg. 3 with the labels of round d-1);
-//  4. sort the accepted hubs and append them to the new frontier.
-// A vertex whose unique candidates exceed cand_limit goes to the next tier.
-__global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
-    extern __shared__ uint32_t sm[];
-    const int lane = lane_id(), wib = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int S_CAP = 1 << p.log_s, M_CAP = 1 << p.log_m, ACC = p.cand_limit;
-    volatile int* wsc = reinterpret_cast<volatile int*>(sm) + wib * 4;
-    uint32_t* S = sm + 4 * nwarps + wib * (S_CAP + M_CAP + ACC);
-    uint32_t* M = S + S_CAP;
-    uint32_t* acc = M + M_CAP;
-    unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
-    const int nlist = *p.list_n;
-    for (int i = blockIdx.x * nwarps + wib; i < nlist; i += gridDim.x * nwarps) {
-        __syncwarp();
-        const int32_t v = p.list[i];
-        const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
-        for (int s = lane; s < S_CAP; s += 32) S[s] = kEmpty;
-        for (int s = lane; s < M_CAP; s += 32) M[s] = kEmpty;
-        if (lane == 0) {
-            wsc[0] = 0;
-            wsc[1] = 0;
-            wsc[2] = 0;
-        }
-        __syncwarp();
-        for (int64_t j = lane; j < ll; j += 32) map_insert(M, p.log_m, p.lent[lb + j]);
-        c_staged += ll;
-        __syncwarp();
-        const int64_t nb = p.roff[v], ne = p.roff[v + 1];
-        c_arcs += ne - nb;
-        bool ovf = false;
-        for (int64_t base = nb; base < ne && !ovf; base += 32) {
-            const int64_t j = base + lane;
-            int cnt = 0;
-            int64_t st = 0;
-            if (j < ne) {
-                const uint64_t f = p.fse[p.rcol[j]];
-                st = (int64_t)fstart(f);
-                cnt = (int)fcount(f);
-            }
-            const int incl = warp_incl_scan(cnt, lane);
-            const int total = __shfl_sync(kFull, incl, 31);
-            const int excl = incl - cnt;
-            c_msgs += total;
-            for (int ib = 0; ib < total; ib += 32) {
-                const int it = ib + lane;
-                const int k = warp_owner(excl, it);
-                const int64_t stk = __shfl_sync(kFull, st, k);
-                const int exk = __shfl_sync(kFull, excl, k);
-                if (it < total) {
-                    const uint32_t h = p.fhub[stk + (it - exk)];
-                    if (h < (uint32_t)v && map_find(M, p.log_m, h) == kEmpty) {
-                        if (wsc[0] >= p.cand_limit) {
-                            wsc[1] = 1;
-                        } else if (set_insert(S, p.log_s, h)) {
-                            atomicAdd((int*)&wsc[0], 1);
-                        }
-                    }
-                }
-                __syncwarp();
-                if (wsc[1]) {
-                    ovf = true;
-                    break;
-                }
-            }
-        }
-        __syncwarp();
-        if (ovf || wsc[0] > p.cand_limit) {
-            if (lane == 0) {
-                const int o = atomicAdd(p.esc_n, 1);
-                p.esc[o] = v;
-            }
-            continue;
-        }
-        c_vert += 1;
-        c_uniq += wsc[0];
-        // distance checks
-        for (int sb = 0; sb < S_CAP; sb += 32) {
-            const uint32_t h = S[sb + lane];
-            const bool has = h != kEmpty;
-            unsigned mask = __ballot_sync(kFull, has);
-            int64_t hb = 0, he = 0;
-            if (has) {
-                hb = p.loff[h];
-                he = p.loff[h + 1];
-            }
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const uint32_t hh = __shfl_sync(kFull, h, src);
-                const int64_t b = __shfl_sync(kFull, hb, src), e = __shfl_sync(kFull, he, src);
-                bool wit = false;
-                for (int64_t jb = b; jb < e; jb += 32) {
-                    const int64_t jj = jb + lane;
-                    bool hit = false;
-                    if (jj < e) {
-                        const uint32_t x = p.lent[jj];
-                        const uint32_t dv = map_find(M, p.log_m, hub_of(x));
-                        hit = dv != kEmpty && dv + dist_of(x) <= p.d;
-                    }
-                    c_probed += (unsigned long long)min((int64_t)32, e - jb);
-                    if (__any_sync(kFull, hit)) {
-                        wit = true;
-                        break;
-                    }
-                }
-                if (!wit && lane == 0) {
-                    const int q = wsc[2];
-                    acc[q] = hh;
-                    wsc[2] = q + 1;
-                }
-            }
-        }
-        __syncwarp();
-        const int nacc = wsc[2];
-        if (nacc > 0) {
-            int P = 1;
-            while (P < nacc) P <<= 1;
-            for (int s = nacc + lane; s < P; s += 32) acc[s] = kEmpty;
-            __syncwarp();
-            group_bitonic_sort(acc, P, lane, 32, WarpSync());
-            unsigned long long start = 0;
-            if (lane == 0) start = atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
-            start = __shfl_sync(kFull, start, 0);
-            if (start + nacc <= p.fcap) {
-                for (int j = lane; j < nacc; j += 32) p.fhub_new[start + j] = acc[j];
-                if (lane == 0) p.fse_new[v] = fpack(start, (uint32_t)nacc);
-            } else if (lane == 0) {
-                p.ctr->fovf = 1;
-            }
-            c_acc += nacc;
-        }
+// Distance check of up to 32 candidates held one per lane (valid lanes).
+// All (candidate, L(h) entry) pairs are spread over the lanes in row order;
+// entry w is a witness when M[w] + d(w,h) <= d (the test of Alg. 3 with the
+// labels of round d-1).  A candidate's remaining entries are skipped once it
+// has a witness.  The last entry of L(h) is (h,0), never a witness (h is not
+// a hub of v), and is not read.  Returns the lanes whose candidate survives.
+__device__ __forceinline__ unsigned check_chunk(const int64_t* loff, const uint32_t* lent, const uint32_t* M,
+                                                int log_m, uint32_t d, uint32_t h, bool valid, unsigned* pm_sm,
+                                                unsigned long long& probed) {
+    const int lane = threadIdx.x & 31;
+    int64_t hb = 0;
+    int hl = 0;
+    if (valid) {
+        hb = loff[h];
+        hl = (int)(loff[h + 1] - hb) - 1;
     }
-    if (lane == 0) {
-        // per-lane counters that every lane accumulated identically: count once
-        atomicAdd(&p.ctr->arcs, c_arcs);
-        atomicAdd(&p.ctr->msgs, c_msgs);
-        atomicAdd(&p.ctr->uniq, c_uniq);
-        atomicAdd(&p.ctr->staged, c_staged);
-        atomicAdd(&p.ctr->probed, c_probed);
-        atomicAdd(&p.ctr->accepted, c_acc);
-        atomicAdd(&p.ctr->tier[0], c_vert);
+    const unsigned vmask = __ballot_sync(kFull, valid);
+    if (lane == 0) *pm_sm = 0;
+    const int incl = warp_incl_scan(hl, lane);
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - hl;
+    __syncwarp();
+    for (int ib = 0; ib < total; ib += 32) {
+        const unsigned pm = *(volatile unsigned*)pm_sm;
+        if ((pm & vmask) == vmask) break;
+        const int it = ib + lane;
+        const int k = warp_owner(excl, it);
+        const int64_t hbk = __shfl_sync(kFull, hb, k);
+        const int exk = __shfl_sync(kFull, excl, k);
+        if (it < total && !((pm >> k) & 1u)) {
+            const uint32_t x = lent[hbk + (it - exk)];
+            const uint32_t dv = map_find(M, log_m, hub_of(x));
+            ++probed;
+            if (dv != kEmpty && dv + dist_of(x) <= d) atomicOr(pm_sm, 1u << k);
+        }
+        __syncwarp();
     }
+    const unsigned pm = *(volatile unsigned*)pm_sm;
+    __syncwarp();
+    return vmask & ~pm;
 }
 
-// One block per vertex; tables either in shared memory (kGlobal = false) or
-// in this block's slice of global scratch sized for the vertex (kGlobal).
-template <bool kGlobal>
-__device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, int log_s_max, int log_m_max,
-                                int acc_max, int* sh, unsigned long long* cnt) {
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
-    const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
-    const int64_t nb = p.roff[v], ne = p.roff[v + 1];
-    int log_m = ceil_log2_i64(2 * ll + 2 * nthr);
-    if (log_m < 5) log_m = 5;
-    int log_s = log_s_max, acc_cap = acc_max;
-    if (kGlobal) {
-        // bound on unique candidates: min(v, sum of frontier sizes of the neighbours)
-        if (tid == 0) sh[3] = 0;
-        __syncthreads();
-        int64_t part = 0;
-        for (int64_t j = nb + tid; j < ne; j += nthr) part += fcount(p.fse[p.rcol[j]]);
-        part = warp_sum(part);
-        if (lane == 0) atomicAdd((unsigned long long*)(sh + 4), (unsigned long long)part);
-        __syncthreads();
-        int64_t bound = (int64_t)(*(unsigned long long*)(sh + 4));
-        if (bound > v) bound = v;
-        log_s = ceil_log2_i64(2 * bound + 2 * nthr);
-        if (log_s < 5) log_s = 5;
-        acc_cap = 1 << ceil_log2_i64(bound + 1);
-        __syncthreads();
-        if (tid == 0) *(unsigned long long*)(sh + 4) = 0;
-    } else if (log_m > log_m_max) {
-        if (tid == 0) {
-            const int o = atomicAdd(p.esc_n, 1);
-            p.esc[o] = v;
-        }
-        return;
-    }
-    const int S_CAP = 1 << log_s, M_CAP = 1 << log_m;
-    const int limit = kGlobal ? acc_cap : p.cand_limit;
-    uint32_t* S = tabs;
-    uint32_t* M = S + S_CAP;
-    uint32_t* acc = M + M_CAP;
-    for (int s = tid; s < S_CAP; s += nthr) S[s] = kEmpty;
-    for (int s = tid; s < M_CAP; s += nthr) M[s] = kEmpty;
-    if (tid == 0) {
-        sh[0] = 0;  // unique count
-        sh[1] = 0;  // overflow
-        sh[2] = 0;  // accepted count
-    }
-    __syncthreads();
-    for (int64_t j = tid; j < ll; j += nthr) map_insert(M, log_m, p.lent[lb + j]);
-    __syncthreads();
-    volatile int* vsh = sh;
-    // gather: warp w handles neighbour chunks w, w + nw, ...
-    bool stop = false;
-    for (int64_t base = nb + 32 * wid; base < ne && !stop; base += 32 * nw) {
+// Gather of v's messages into the set S: for every neighbour a and every h in
+// dL_{d-1}(a) with h < v and h not already a hub of v (not in M).  Warp-level
+// load-balanced expansion over 32 neighbours at a time.  Stops (returns
+// false) when the set would exceed `limit` entries.
+__device__ __forceinline__ bool gather_warp(const GpParams& p, int32_t v, int64_t nb, int64_t ne, int64_t stride,
+                                            uint32_t* S, int log_s, const uint32_t* M, int log_m, int limit,
+                                            int* cnt_sm, volatile int* ovf_sm, unsigned long long& msgs) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = nb; base < ne; base += stride) {
         const int64_t j = base + lane;
         int c = 0;
         int64_t st = 0;
@@ -438,7 +295,7 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, in
         const int incl = warp_incl_scan(c, lane);
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - c;
-        if (lane == 0) cnt[1] += total;
+        msgs += (lane == 0) ? (unsigned long long)total : 0ull;
         for (int ib = 0; ib < total; ib += 32) {
             const int it = ib + lane;
             const int k = warp_owner(excl, it);
@@ -447,22 +304,177 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, in
             if (it < total) {
                 const uint32_t h = p.fhub[stk + (it - exk)];
                 if (h < (uint32_t)v && map_find(M, log_m, h) == kEmpty) {
-                    if (vsh[0] >= limit) {
-                        vsh[1] = 1;
+                    if (*(volatile int*)cnt_sm >= limit) {
+                        *ovf_sm = 1;
                     } else if (set_insert(S, log_s, h)) {
-                        atomicAdd(&sh[0], 1);
+                        atomicAdd(cnt_sm, 1);
                     }
                 }
             }
-            if (__any_sync(kFull, vsh[1] != 0)) {
-                stop = true;
-                break;
-            }
+            if (__any_sync(kFull, *ovf_sm != 0)) return false;
         }
     }
+    return true;
+}
+
+// One warp per vertex (tables in shared memory):
+//  1. stage L(v) into the hub-keyed map M;
+//  2. gather the unique messages into the set S;
+//  3. check them 32 at a time (check_chunk);
+//  4. sort the accepted hubs and append them to the new frontier.
+// A vertex whose unique candidates exceed cand_limit goes to the block tier.
+__global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
+    extern __shared__ uint32_t sm[];
+    const int lane = lane_id(), wib = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int S_CAP = 1 << p.log_s, M_CAP = 1 << p.log_m, ACC = p.cand_limit;
+    int* wsc = reinterpret_cast<int*>(sm) + wib * 4;  // [0] unique count [1] overflow [3] pruned mask
+    uint32_t* S = sm + 4 * nwarps + wib * (S_CAP + M_CAP + ACC);
+    uint32_t* M = S + S_CAP;
+    uint32_t* C = M + M_CAP;
+    unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
+    const int nlist = *p.list_n;
+    for (int i = blockIdx.x * nwarps + wib; i < nlist; i += gridDim.x * nwarps) {
+        __syncwarp();
+        const int32_t v = p.list[i];
+        const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
+        for (int s = lane; s < S_CAP; s += 32) S[s] = kEmpty;
+        for (int s = lane; s < M_CAP; s += 32) M[s] = kEmpty;
+        if (lane == 0) {
+            wsc[0] = 0;
+            wsc[1] = 0;
+        }
+        __syncwarp();
+        for (int64_t j = lane; j < ll; j += 32) map_insert(M, p.log_m, p.lent[lb + j]);
+        __syncwarp();
+        const int64_t nb = p.roff[v], ne = p.roff[v + 1];
+        const bool ok = gather_warp(p, v, nb, ne, 32, S, p.log_s, M, p.log_m, p.cand_limit, &wsc[0],
+                                    (volatile int*)&wsc[1], c_msgs);
+        __syncwarp();
+        const int nS = *(volatile int*)&wsc[0];
+        if (!ok || nS > p.cand_limit) {
+            if (lane == 0) {
+                const int o = atomicAdd(p.esc_n, 1);
+                p.esc[o] = v;
+            }
+            continue;
+        }
+        if (lane == 0) {
+            c_arcs += ne - nb;
+            c_staged += ll;
+            c_vert += 1;
+            c_uniq += nS;
+        }
+        // compact the set into C
+        int nc = 0;
+        for (int sb = 0; sb < S_CAP; sb += 32) {
+            const uint32_t h = S[sb + lane];
+            const bool has = h != kEmpty;
+            const unsigned m = __ballot_sync(kFull, has);
+            if (has) C[nc + __popc(m & ((1u << lane) - 1u))] = h;
+            nc += __popc(m);
+        }
+        __syncwarp();
+        // distance checks, 32 candidates at a time; survivors compacted in place
+        int nacc = 0;
+        for (int cb = 0; cb < nc; cb += 32) {
+            const bool valid = cb + lane < nc;
+            const uint32_t h = valid ? C[cb + lane] : 0u;
+            __syncwarp();
+            const unsigned okm = check_chunk(p.loff, p.lent, M, p.log_m, p.d, h, valid, (unsigned*)&wsc[3], c_probed);
+            if ((okm >> lane) & 1u) C[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
+            nacc += __popc(okm);
+            __syncwarp();
+        }
+        if (nacc > 0) {
+            int P = 1;
+            while (P < nacc) P <<= 1;
+            for (int s = nacc + lane; s < P; s += 32) C[s] = kEmpty;
+            __syncwarp();
+            group_bitonic_sort(C, P, lane, 32, WarpSync());
+            unsigned long long start = 0;
+            if (lane == 0) start = atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
+            start = __shfl_sync(kFull, start, 0);
+            if (start + nacc <= p.fcap) {
+                for (int j = lane; j < nacc; j += 32) p.fhub_new[start + j] = C[j];
+                if (lane == 0) p.fse_new[v] = fpack(start, (uint32_t)nacc);
+            } else if (lane == 0) {
+                p.ctr->fovf = 1;
+            }
+            if (lane == 0) c_acc += nacc;
+        }
+    }
+    c_probed = warp_sum(c_probed);
+    c_msgs = warp_sum(c_msgs);
+    if (lane == 0) {
+        atomicAdd(&p.ctr->arcs, c_arcs);
+        atomicAdd(&p.ctr->msgs, c_msgs);
+        atomicAdd(&p.ctr->uniq, c_uniq);
+        atomicAdd(&p.ctr->staged, c_staged);
+        atomicAdd(&p.ctr->probed, c_probed);
+        atomicAdd(&p.ctr->accepted, c_acc);
+        atomicAdd(&p.ctr->tier[0], c_vert);
+    }
+}
+
+// Block-per-vertex scalars in shared memory (ints)
+enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_BOUND = 4 /* 2 ints */, SH_START = 6 /* 2 ints */,
+       SH_PM = 16 /* one word per warp */, SH_WORDS = 48 };
+
+// One block per vertex; tables either in shared memory (kGlobal = false) or
+// in this block's slice of global scratch sized for the vertex (kGlobal).
+template <bool kGlobal>
+__device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, int log_s_max, int log_m_max,
+                                int* sh, unsigned long long* cnt) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
+    const int64_t nb = p.roff[v], ne = p.roff[v + 1];
+    int log_m = ceil_log2_i64(2 * ll + 2 * nthr);
+    if (log_m < 5) log_m = 5;
+    int log_s = log_s_max, cap = p.cand_limit;
+    if (kGlobal) {
+        // bound on unique candidates: min(v, sum of frontier sizes of the neighbours)
+        int64_t part = 0;
+        for (int64_t j = nb + tid; j < ne; j += nthr) part += fcount(p.fse[p.rcol[j]]);
+        part = warp_sum(part);
+        if (lane == 0) atomicAdd((unsigned long long*)(sh + SH_BOUND), (unsigned long long)part);
+        __syncthreads();
+        int64_t bound = (int64_t)(*(volatile unsigned long long*)(sh + SH_BOUND));
+        if (bound > v) bound = v;
+        log_s = ceil_log2_i64(2 * bound + 2 * nthr);
+        if (log_s < 5) log_s = 5;
+        cap = 1 << ceil_log2_i64(bound + 1);
+        __syncthreads();
+        if (tid == 0) *(unsigned long long*)(sh + SH_BOUND) = 0;
+    } else if (log_m > log_m_max) {
+        if (tid == 0) {
+            const int o = atomicAdd(p.esc_n, 1);
+            p.esc[o] = v;
+        }
+        return;
+    }
+    const int S_CAP = 1 << log_s, M_CAP = 1 << log_m;
+    uint32_t* S = tabs;
+    uint32_t* M = S + S_CAP;
+    uint32_t* C = M + M_CAP;
+    for (int s = tid; s < S_CAP; s += nthr) S[s] = kEmpty;
+    for (int s = tid; s < M_CAP; s += nthr) M[s] = kEmpty;
+    if (tid == 0) {
+        sh[SH_UNIQ] = 0;
+        sh[SH_OVF] = 0;
+        sh[SH_ACC] = 0;
+        sh[SH_NC] = 0;
+    }
     __syncthreads();
-    const int nS = vsh[0];
-    if (vsh[1] || nS > limit) {
+    for (int64_t j = tid; j < ll; j += nthr) map_insert(M, log_m, p.lent[lb + j]);
+    __syncthreads();
+    // gather: warp w handles neighbour chunks w, w + nw, ...
+    gather_warp(p, v, nb + 32 * wid, ne, 32 * nw, S, log_s, M, log_m, cap, &sh[SH_UNIQ],
+                (volatile int*)&sh[SH_OVF], cnt[1]);
+    __syncthreads();
+    const int nS = *(volatile int*)&sh[SH_UNIQ];
+    if (*(volatile int*)&sh[SH_OVF] || nS > cap) {
         __syncthreads();
         if (tid == 0) {
             const int o = atomicAdd(p.esc_n, 1);
@@ -476,58 +488,44 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, in
         cnt[3] += ll;
         cnt[6] += 1;
     }
-    // distance checks: warp w takes slot chunks w, w + nw, ...
+    // compact the set into C (any order)
     for (int sb = 32 * wid; sb < S_CAP; sb += 32 * nw) {
         const uint32_t h = S[sb + lane];
         const bool has = h != kEmpty;
-        unsigned mask = __ballot_sync(kFull, has);
-        int64_t hb = 0, he = 0;
-        if (has) {
-            hb = p.loff[h];
-            he = p.loff[h + 1];
-        }
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const uint32_t hh = __shfl_sync(kFull, h, src);
-            const int64_t b = __shfl_sync(kFull, hb, src), e = __shfl_sync(kFull, he, src);
-            bool wit = false;
-            for (int64_t jb = b; jb < e; jb += 32) {
-                const int64_t jj = jb + lane;
-                bool hit = false;
-                if (jj < e) {
-                    const uint32_t x = p.lent[jj];
-                    const uint32_t dv = map_find(M, log_m, hub_of(x));
-                    hit = dv != kEmpty && dv + dist_of(x) <= p.d;
-                }
-                if (lane == 0) cnt[4] += (unsigned long long)min((int64_t)32, e - jb);
-                if (__any_sync(kFull, hit)) {
-                    wit = true;
-                    break;
-                }
-            }
-            if (!wit && lane == 0) {
-                const int q = atomicAdd(&sh[2], 1);
-                acc[q] = hh;
-            }
-        }
+        const unsigned m = __ballot_sync(kFull, has);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&sh[SH_NC], __popc(m));
+        base = __shfl_sync(kFull, base, 0);
+        if (has) C[base + __popc(m & ((1u << lane) - 1u))] = h;
     }
     __syncthreads();
-    const int nacc = vsh[2];
+    const int nc = *(volatile int*)&sh[SH_NC];
+    // distance checks: warp w takes candidate chunks w, w + nw, ...; a
+    // rejected candidate's slot is overwritten with kEmpty
+    for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
+        const bool valid = cb + lane < nc;
+        const uint32_t h = valid ? C[cb + lane] : 0u;
+        const unsigned okm = check_chunk(p.loff, p.lent, M, log_m, p.d, h, valid, (unsigned*)&sh[SH_PM + wid],
+                                         cnt[4]);
+        if (valid && !((okm >> lane) & 1u)) C[cb + lane] = kEmpty;
+        if (lane == 0 && okm) atomicAdd(&sh[SH_ACC], __popc(okm));
+    }
+    __syncthreads();
+    const int nacc = *(volatile int*)&sh[SH_ACC];
     if (nacc > 0) {
         int P = 1;
-        while (P < nacc) P <<= 1;
-        for (int s = nacc + tid; s < P; s += nthr) acc[s] = kEmpty;
+        while (P < nc) P <<= 1;
+        for (int s = nc + tid; s < P; s += nthr) C[s] = kEmpty;
         __syncthreads();
-        group_bitonic_sort(acc, P, tid, nthr, BlockSync());
+        group_bitonic_sort(C, P, tid, nthr, BlockSync());  // accepted hubs first, kEmpty last
         if (tid == 0) {
             const unsigned long long start = atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
-            *(unsigned long long*)(sh + 6) = start;
+            *(unsigned long long*)(sh + SH_START) = start;
         }
         __syncthreads();
-        const unsigned long long start = *(volatile unsigned long long*)(sh + 6);
+        const unsigned long long start = *(volatile unsigned long long*)(sh + SH_START);
         if (start + nacc <= p.fcap) {
-            for (int j = tid; j < nacc; j += nthr) p.fhub_new[start + j] = acc[j];
+            for (int j = tid; j < nacc; j += nthr) p.fhub_new[start + j] = C[j];
             if (tid == 0) p.fse_new[v] = fpack(start, (uint32_t)nacc);
         } else if (tid == 0) {
             p.ctr->fovf = 1;
@@ -537,16 +535,9 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, in
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_gp_block(GpParams p) {
-    extern __shared__ uint32_t sm[];
-    int* sh = reinterpret_cast<int*>(sm);            // 16 ints of scalars
-    uint32_t* tabs = sm + 16;
-    unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
-    const int n1 = *p.list_n;
-    for (int i = blockIdx.x; i < n1; i += gridDim.x) {
-        gp_block_vertex<false>(p, p.list[i], tabs, p.log_s, p.log_m, p.cand_limit, sh, cnt);
-        __syncthreads();
-    }
+__device__ __forceinline__ void flush_block_counters(const GpParams& p, unsigned long long* cnt, int tier) {
+    cnt[1] = warp_sum(cnt[1]);
+    cnt[4] = warp_sum(cnt[4]);
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&p.ctr->msgs, cnt[1]);
         atomicAdd(&p.ctr->probed, cnt[4]);
@@ -556,32 +547,35 @@ __global__ void __launch_bounds__(1024) k_gp_block(GpParams p) {
         atomicAdd(&p.ctr->uniq, cnt[2]);
         atomicAdd(&p.ctr->staged, cnt[3]);
         atomicAdd(&p.ctr->accepted, cnt[5]);
-        atomicAdd(&p.ctr->tier[1], cnt[6]);
+        atomicAdd(&p.ctr->tier[tier], cnt[6]);
     }
 }
 
-__global__ void __launch_bounds__(1024) k_gp_global(GpParams p) {
-    __shared__ __align__(8) int sh[16];
+__global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
+    extern __shared__ uint32_t sm[];
+    int* sh = reinterpret_cast<int*>(sm);
+    uint32_t* tabs = sm + SH_WORDS;
+    unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int n1 = *p.list_n;
+    for (int i = blockIdx.x; i < n1; i += gridDim.x) {
+        gp_block_vertex<false>(p, p.list[i], tabs, p.log_s, p.log_m, sh, cnt);
+        __syncthreads();
+    }
+    flush_block_counters(p, cnt, 1);
+}
+
+__global__ void __launch_bounds__(512) k_gp_global(GpParams p) {
+    __shared__ __align__(8) int sh[SH_WORDS];
     unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
     const int n2 = *p.list_n;
     uint32_t* tabs = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
-    if (threadIdx.x == 0) *(unsigned long long*)(sh + 4) = 0;
+    if (threadIdx.x == 0) *(unsigned long long*)(sh + SH_BOUND) = 0;
     __syncthreads();
     for (int i = blockIdx.x; i < n2; i += gridDim.x) {
-        gp_block_vertex<true>(p, p.list[i], tabs, 0, 0, 0, sh, cnt);
+        gp_block_vertex<true>(p, p.list[i], tabs, 0, 0, sh, cnt);
         __syncthreads();
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&p.ctr->msgs, cnt[1]);
-        atomicAdd(&p.ctr->probed, cnt[4]);
-    }
-    if (threadIdx.x == 0) {
-        atomicAdd(&p.ctr->arcs, cnt[0]);
-        atomicAdd(&p.ctr->uniq, cnt[2]);
-        atomicAdd(&p.ctr->staged, cnt[3]);
-        atomicAdd(&p.ctr->accepted, cnt[5]);
-        atomicAdd(&p.ctr->tier[2], cnt[6]);
-    }
+    flush_block_counters(p, cnt, 2);
 }
 
 // ------------------------------------------------------------ merge

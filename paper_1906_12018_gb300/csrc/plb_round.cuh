@@ -17,10 +17,11 @@ __global__ void k_init(const int64_t* roff, int64_t n, int64_t* loff, uint32_t* 
 __global__ void k_active_degree(const int64_t* roff, const int32_t* A, const RoundCounters* ctr, int64_t* adeg,
                                 int64_t n);
 __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t* fse, const uint32_t* fhub,
-                       const int32_t* A, const int64_t* aoff, const RoundCounters* ctr, uint8_t* recv, int64_t n);
-__global__ void k_collect(uint8_t* recv, const int64_t* roff, const int64_t* loff, int64_t n, uint64_t* fse_new,
-                          int32_t* R, int32_t* O1, RoundCounters* ctr, int64_t warp_label_limit,
-                          int64_t warp_deg_limit);
+                       const int32_t* A, const int64_t* aoff, const RoundCounters* ctr, unsigned long long* recv,
+                       int64_t n);
+__global__ void k_collect(unsigned long long* recv, const int64_t* roff, const int64_t* loff, int64_t n,
+                          uint64_t* fse_new, int32_t* R, int32_t* O1, int32_t* O2, RoundCounters* ctr,
+                          TierLimits lim);
 __global__ void k_after_collect(RoundCounters* ctr);
 __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n);
 __global__ void k_gp_warp(GpParams p);
