@@ -238,6 +238,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     // ------------------------------------------------------------ rounds
     int status = PLB_OK;
     int d = 0;
+    std::vector<std::pair<int, cudaEvent_t>> round_ev;  // (round, start event)
     for (;;) {
         ++d;
         const int nxt = cur ^ 1;
@@ -350,6 +351,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         if (d < PLB_MAX_ROUNDS) {
             st.receivers[d] = (int64_t)hctr->nR + hctr->nO1_base + hctr->nO2_base;
             st.accepted[d] = acc;
+            st.unique_round[d] = (int64_t)hctr->uniq;
+            st.probed_round[d] = (int64_t)hctr->probed;
+            st.messages_round[d] = (int64_t)hctr->msgs;
+            if (tm.on) round_ev.push_back({d, r0});
         }
         st.arcs_scanned += (int64_t)hctr->arcs;
         st.messages += (int64_t)hctr->msgs;
@@ -445,6 +450,12 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         st.ms_merge = tm.total(T_MERGE);
         st.ms_finalize = tm.total(T_FINAL);
         st.ms_total = tm.total(T_ALL);
+        for (size_t i = 0; i < round_ev.size(); ++i) {
+            cudaEvent_t end = i + 1 < round_ev.size() ? round_ev[i + 1].second : f0;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, round_ev[i].second, end);
+            st.ms_round[round_ev[i].first] = ms;
+        }
     }
     L->stats = st;
     *out = L;

@@ -189,7 +189,7 @@ __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const i
             const int64_t ll = loff[v + 1] - loff[v];
             const int64_t deg = roff[v + 1] - roff[v];
             if ((int64_t)bound <= lim.warp_bound && ll <= lim.warp_label && deg <= lim.warp_deg) tier = 0;
-            else if ((int64_t)bound <= lim.block_cand && ll <= lim.block_label) tier = 1;
+            else if (ll <= lim.block_label) tier = 1;
             else tier = 2;
         }
         const unsigned am = __activemask();
@@ -500,24 +500,28 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, in
     }
     __syncthreads();
     const int nc = *(volatile int*)&sh[SH_NC];
-    // distance checks: warp w takes candidate chunks w, w + nw, ...; a
-    // rejected candidate's slot is overwritten with kEmpty
+    // distance checks: warp w takes candidate chunks w, w + nw, ...; the
+    // accepted hubs are appended to A (the set's storage, free by now)
+    uint32_t* Acc = S;
     for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
         const bool valid = cb + lane < nc;
         const uint32_t h = valid ? C[cb + lane] : 0u;
         const unsigned okm = check_chunk(p.loff, p.lent, M, log_m, p.d, h, valid, (unsigned*)&sh[SH_PM + wid],
                                          cnt[4]);
-        if (valid && !((okm >> lane) & 1u)) C[cb + lane] = kEmpty;
-        if (lane == 0 && okm) atomicAdd(&sh[SH_ACC], __popc(okm));
+        int base = 0;
+        if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
+        base = __shfl_sync(kFull, base, 0);
+        if ((okm >> lane) & 1u) Acc[base + __popc(okm & ((1u << lane) - 1u))] = h;
     }
     __syncthreads();
     const int nacc = *(volatile int*)&sh[SH_ACC];
     if (nacc > 0) {
         int P = 1;
-        while (P < nc) P <<= 1;
-        for (int s = nc + tid; s < P; s += nthr) C[s] = kEmpty;
+        while (P < nacc) P <<= 1;
+        for (int s = nacc + tid; s < P; s += nthr) Acc[s] = kEmpty;
         __syncthreads();
-        group_bitonic_sort(C, P, tid, nthr, BlockSync());  // accepted hubs first, kEmpty last
+        group_bitonic_sort(Acc, P, tid, nthr, BlockSync());
+        C = Acc;
         if (tid == 0) {
             const unsigned long long start = atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
             *(unsigned long long*)(sh + SH_START) = start;

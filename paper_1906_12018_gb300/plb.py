@@ -80,6 +80,10 @@ class BuildStats(ctypes.Structure):
         ("total_labels", ctypes.c_int64),
         ("receivers", ctypes.c_int64 * MAX_ROUNDS),
         ("accepted", ctypes.c_int64 * MAX_ROUNDS),
+        ("unique_round", ctypes.c_int64 * MAX_ROUNDS),
+        ("probed_round", ctypes.c_int64 * MAX_ROUNDS),
+        ("messages_round", ctypes.c_int64 * MAX_ROUNDS),
+        ("ms_round", ctypes.c_double * MAX_ROUNDS),
         ("arcs_scanned", ctypes.c_int64),
         ("messages", ctypes.c_int64),
         ("unique_candidates", ctypes.c_int64),
@@ -105,6 +109,10 @@ class BuildStats(ctypes.Structure):
             "total_labels": self.total_labels,
             "receivers": list(self.receivers[1 : r + 1]),
             "accepted": list(self.accepted[1 : r + 1]),
+            "unique_round": list(self.unique_round[1 : r + 1]),
+            "probed_round": list(self.probed_round[1 : r + 1]),
+            "messages_round": list(self.messages_round[1 : r + 1]),
+            "ms_round": list(self.ms_round[1 : r + 1]),
             "arcs_scanned": self.arcs_scanned,
             "messages": self.messages,
             "unique_candidates": self.unique_candidates,
