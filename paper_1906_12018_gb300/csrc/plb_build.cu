@@ -202,6 +202,30 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     st.launches += 1;
     int64_t T = n;  // labels so far
     int cur = 0;    // index of current L and previous frontier
+    // probe index of L (hub-keyed table per long row), rebuilt after each merge
+    int64_t* hoff = pool.alloc<int64_t>(n + 1);
+    int64_t hcap = std::max<int64_t>(4 * n, 1024);
+    uint32_t* htab = pool.alloc<uint32_t>(hcap);
+    PLB_ALLOC_OK();
+    auto build_index = [&](int which, int64_t total) -> int {
+        if (4 * total > hcap) {
+            pool.release(htab);
+            hcap = 4 * total + total / 2 + 1024;
+            htab = pool.alloc<uint32_t>(hcap);
+            if (pool.failed) return PLB_ERR_OOM;
+        }
+        k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[which], n, tmp64);
+        if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
+        k_index_clear<<<flat_grid_cap, kFlatThreads, 0, s>>>(htab, hoff + n);
+        k_index_fill<<<grid_for((total + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(loff[which],
+                                                                                             lent[which], hoff, htab, n);
+        st.launches += 5;
+        return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
+    };
+    {
+        const int e = build_index(0, T);
+        if (e != PLB_OK) return e;
+    }
     if (tm.on) tm.span(T_PREP, t0, tm.mark());
 
     // tier geometry
@@ -280,6 +304,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             p.fcap = (unsigned long long)fcap[nxt];
             p.ctr = ctr;
             p.d = (uint32_t)d;
+            p.hoff = hoff;
+            p.htab = htab;
             if (rerun) {
                 k_rerun_reset<<<gflat, kFlatThreads, 0, s>>>(ctr, fse[nxt], n);
                 st.launches += 1;
@@ -384,9 +410,13 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], A, ctr, (uint32_t)d);
         PLB_CK(cudaGetLastError());
         st.launches += 5;
-        if (tm.on) tm.span(T_MERGE, m0, tm.mark());
         T = Tn;
         cur = nxt;
+        {
+            const int e = build_index(cur, T);
+            if (e != PLB_OK) return e;
+        }
+        if (tm.on) tm.span(T_MERGE, m0, tm.mark());
         // round-start reset of the per-round counters (nA carries over)
         PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
         PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));

@@ -52,7 +52,12 @@ struct GpParams {
     int label_limit;           // max |L(v)| (block tier: escalate beyond)
     uint32_t* gscratch;        // global tier: per-block table storage
     int64_t gscratch_words;    // words per block
+    const int64_t* hoff;       // probe index of L: per row a hub-keyed table (empty rows: none)
+    const uint32_t* htab;
 };
+
+// Rows of L with at least this many entries get a hub-keyed probe table.
+constexpr int kIndexMinLen = 16;
 
 // Routing limits of k_collect (see the tier geometry in build_core).
 struct TierLimits {

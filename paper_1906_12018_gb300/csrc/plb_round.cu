@@ -234,39 +234,65 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
 
 // ------------------------------------------------------- gather + prune
 // Distance check of up to 32 candidates held one per lane (valid lanes).
-// All (candidate, L(h) entry) pairs are spread over the lanes in row order;
-// entry w is a witness when M[w] + d(w,h) <= d (the test of Alg. 3 with the
-// labels of round d-1).  A candidate's remaining entries are skipped once it
-// has a witness.  The last entry of L(h) is (h,0), never a witness (h is not
-// a hub of v), and is not read.  Returns the lanes whose candidate survives.
-__device__ __forceinline__ unsigned check_chunk(const int64_t* loff, const uint32_t* lent, const uint32_t* M,
-                                                int log_m, uint32_t d, uint32_t h, bool valid, unsigned* pm_sm,
+// A witness for candidate h is a hub w of both v and h with
+// d(w,v) + d(w,h) <= d (the test of Alg. 3 with the labels of round d-1).
+// Each candidate scans the shorter side:
+//   A: the entries of L(h) (its last entry, (h,0), is never a witness and is
+//      skipped), each probed in the shared-memory map M of L(v);
+//   B: the entries of L(v) with hub < h (only those can be hubs of h), each
+//      probed in h's row of the global probe index (rows of >= 16 entries).
+// All (candidate, entry) pairs are spread over the lanes; a candidate's
+// remaining entries are skipped once it has a witness.  Returns the lanes
+// whose candidate survives.
+__device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_t* M, int log_m, const uint32_t* lv,
+                                                int64_t lvlen, uint32_t h, bool valid, unsigned* pm_sm,
                                                 unsigned long long& probed) {
     const int lane = threadIdx.x & 31;
-    int64_t hb = 0;
-    int hl = 0;
+    int64_t base = 0;  // A: start of L(h); B: start of h's probe table
+    int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
     if (valid) {
-        hb = loff[h];
-        hl = (int)(loff[h + 1] - hb) - 1;
+        const int64_t hb = p.loff[h];
+        const int la = (int)(p.loff[h + 1] - hb) - 1;
+        base = hb;
+        items = la;
+        const int64_t x0 = p.hoff[h], x1 = p.hoff[h + 1];
+        if (x1 > x0) {
+            const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
+            if (2 * lb < la) {
+                items = lb;
+                base = x0;
+                meta = __ffs((int)(x1 - x0));  // log2 + 1
+            }
+        }
     }
     const unsigned vmask = __ballot_sync(kFull, valid);
     if (lane == 0) *pm_sm = 0;
-    const int incl = warp_incl_scan(hl, lane);
+    const int incl = warp_incl_scan(items, lane);
     const int total = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - hl;
+    const int excl = incl - items;
     __syncwarp();
     for (int ib = 0; ib < total; ib += 32) {
         const unsigned pm = *(volatile unsigned*)pm_sm;
         if ((pm & vmask) == vmask) break;
         const int it = ib + lane;
         const int k = warp_owner(excl, it);
-        const int64_t hbk = __shfl_sync(kFull, hb, k);
+        const int64_t bk = __shfl_sync(kFull, base, k);
         const int exk = __shfl_sync(kFull, excl, k);
+        const int mk = __shfl_sync(kFull, meta, k);
         if (it < total && !((pm >> k) & 1u)) {
-            const uint32_t x = lent[hbk + (it - exk)];
-            const uint32_t dv = map_find(M, log_m, hub_of(x));
+            const int j = it - exk;
+            bool hit = false;
+            if (mk == 0) {
+                const uint32_t x = p.lent[bk + j];
+                const uint32_t dv = map_find(M, log_m, hub_of(x));
+                hit = dv != kEmpty && dv + dist_of(x) <= p.d;
+            } else {
+                const uint32_t y = lv[j];
+                const uint32_t dh = map_find(p.htab + bk, mk - 1, hub_of(y));
+                hit = dh != kEmpty && dh + dist_of(y) <= p.d;
+            }
             ++probed;
-            if (dv != kEmpty && dv + dist_of(x) <= d) atomicOr(pm_sm, 1u << k);
+            if (hit) atomicOr(pm_sm, 1u << k);
         }
         __syncwarp();
     }
@@ -381,7 +407,7 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p.loff, p.lent, M, p.log_m, p.d, h, valid, (unsigned*)&wsc[3], c_probed);
+            const unsigned okm = check_chunk(p, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3], c_probed);
             if ((okm >> lane) & 1u) C[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
@@ -506,8 +532,7 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, in
     for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
         const bool valid = cb + lane < nc;
         const uint32_t h = valid ? C[cb + lane] : 0u;
-        const unsigned okm = check_chunk(p.loff, p.lent, M, log_m, p.d, h, valid, (unsigned*)&sh[SH_PM + wid],
-                                         cnt[4]);
+        const unsigned okm = check_chunk(p, M, log_m, p.lent + lb, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4]);
         int base = 0;
         if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
         base = __shfl_sync(kFull, base, 0);
@@ -580,6 +605,44 @@ __global__ void __launch_bounds__(512) k_gp_global(GpParams p) {
         __syncthreads();
     }
     flush_block_counters(p, cnt, 2);
+}
+
+// ------------------------------------------------------------ probe index
+// Table size of row x: 2^ceil(log2(2|L(x)|)) for rows of >= kIndexMinLen
+// entries, else 0 (those rows are always scanned, never probed).
+__global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = loff[x + 1] - loff[x];
+        hsz[x] = l >= kIndexMinLen ? (int64_t(1) << ceil_log2_i64(2 * l)) : 0;
+    }
+}
+
+// htab[0 .. hoff[n]) = kEmpty (size read on the device).
+__global__ void k_index_clear(uint32_t* htab, const int64_t* hoff_n) {
+    const int64_t total = *hoff_n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        htab[i] = kEmpty;
+}
+
+// Insert every entry of an indexed row into its table (tables pre-filled
+// with kEmpty): flat over entries.
+__global__ void k_index_fill(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
+                             int64_t n) {
+    __shared__ int64_t sh_r[2];
+    const int64_t total = loff[n];
+    const int64_t ntiles = (total + kTileItems - 1) / kTileItems;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kTileItems, p1 = min(total, p0 + kTileItems);
+        __syncthreads();
+        if (threadIdx.x == 0) tile_rows(loff, n, p0, p1, &sh_r[0], &sh_r[1]);
+        __syncthreads();
+        const int64_t r0 = sh_r[0], r1 = sh_r[1];
+        for (int64_t q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+            const int64_t x = row_of(loff, r0, r1, q);
+            const int64_t b = hoff[x], sz = hoff[x + 1] - b;
+            if (sz > 0) map_insert(htab + b, __ffs((int)sz) - 1, lent[q]);
+        }
+    }
 }
 
 // ------------------------------------------------------------ merge

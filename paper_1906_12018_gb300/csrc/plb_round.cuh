@@ -27,6 +27,10 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n);
 __global__ void k_gp_warp(GpParams p);
 __global__ void k_gp_block(GpParams p);
 __global__ void k_gp_global(GpParams p);
+__global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz);
+__global__ void k_index_clear(uint32_t* htab, const int64_t* hoff_n);
+__global__ void k_index_fill(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
+                             int64_t n);
 __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int64_t n, int64_t* newlen, int32_t* A,
                               RoundCounters* ctr);
 __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
