@@ -177,6 +177,28 @@ int plb_labels_free(plb_labels* labels);
  * rounded up to a power of two).  Asynchronous on the stream. */
 int plb_degree_order(const plb_csr* g, int32_t* order_out, plb_stream stream);
 
+/* Allocation-free degree order (no counterpart in the paper; a service of
+ * this library).  Same result as plb_degree_order, for callers that cannot
+ * let the library allocate device memory: processes whose device memory is
+ * owned by a host framework's allocator, servers that admit work against a
+ * fixed HBM budget, and latency-critical paths where cudaMalloc/cudaFree may
+ * block or synchronise the device.  It calls no allocating routine: its
+ * scratch is a fixed array of PLB_NOALLOC_MAX_VERTICES 8-byte keys (8 MiB)
+ * inside the library, held on every GPU that loads the library until the
+ * process exits.
+ *   - n > PLB_NOALLOC_MAX_VERTICES -> PLB_ERR_TOO_LARGE, nothing launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - All calls share the one array (each call rewrites the part it uses
+ *     before reading it): calls whose work overlaps on the GPU -- on
+ *     different streams, or from several host threads -- race and must be
+ *     serialised by the caller.
+ *   - Otherwise as plb_degree_order: row_ptr read, order_out (device,
+ *     int32[n]) written, asynchronous on the stream. */
+#define PLB_NOALLOC_MAX_VERTICES (1 << 20)
+int plb_degree_order_noalloc(const plb_csr* g, int32_t* order_out, plb_stream stream);
+
 /* Human-readable status text (static storage). */
 const char* plb_strerror(int status);
 

@@ -165,6 +165,8 @@ def _lib():
     lib.plb_labels_free.restype = I
     lib.plb_degree_order.argtypes = [ctypes.POINTER(CSR), P, P]
     lib.plb_degree_order.restype = I
+    lib.plb_degree_order_noalloc.argtypes = [ctypes.POINTER(CSR), P, P]
+    lib.plb_degree_order_noalloc.restype = I
     lib.plb_strerror.argtypes = [I]
     lib.plb_strerror.restype = ctypes.c_char_p
     lib.plb_version.argtypes = []
@@ -177,7 +179,7 @@ def exported_symbols() -> list[str]:
     """Names of the entry points declared in include/plb.h."""
     return ["plb_default_options", "plb_build", "plb_build_batch", "plb_query_batch", "plb_query_multi",
             "plb_labels_view", "plb_labels_stats", "plb_labels_bytes", "plb_labels_free", "plb_degree_order",
-            "plb_strerror", "plb_version"]
+            "plb_degree_order_noalloc", "plb_strerror", "plb_version"]
 
 
 def _check(code: int, what: str):
@@ -344,6 +346,25 @@ def degree_order(row_ptr: torch.Tensor, stream=None) -> torch.Tensor:
     g = CSR(n, 0, row_ptr.data_ptr(), None)
     _check(_lib().plb_degree_order(ctypes.byref(g), out.data_ptr() if n else None, _stream(stream)),
            "plb_degree_order")
+    return out
+
+
+NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def degree_order_noalloc(row_ptr: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Same as degree_order without any device allocation by the library
+    (fixed 8 MiB scratch, at most NOALLOC_MAX_VERTICES vertices; concurrent
+    calls race on that scratch).  ``out`` may be passed to avoid the output
+    allocation on the Python side too."""
+    _dev(row_ptr, torch.int64, "row_ptr")
+    n = row_ptr.numel() - 1
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=row_ptr.device)
+    _dev(out, torch.int32, "out")
+    g = CSR(n, 0, row_ptr.data_ptr(), None)
+    _check(_lib().plb_degree_order_noalloc(ctypes.byref(g), out.data_ptr() if n else None, _stream(stream)),
+           "plb_degree_order_noalloc")
     return out
 
 
