@@ -138,9 +138,10 @@ int plb_build(const plb_csr* g, const int32_t* vertex_order, const plb_options* 
  * (host arrays gs[k], orders[k] of device pointers; outs[k] host array that
  * receives k label sets).  By Def. 2 a disjoint union's canonical labels,
  * under any order that keeps each part's own order, are the parts' labels,
- * so each outs[i] equals plb_build(&gs[i], orders[i]).  The union of the
- * parts must have fewer than 2^24 vertices.  Errors as plb_build; on error
- * no label set is returned. */
+ * so each outs[i] equals plb_build(&gs[i], orders[i]).  Parts are taken in
+ * consecutive groups whose union has fewer than 2^24 vertices (one round loop
+ * per group; each part itself must have fewer).  Errors as plb_build; on
+ * error no label set is returned. */
 int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k,
                     const plb_options* opt, plb_stream stream, plb_labels** outs);
 

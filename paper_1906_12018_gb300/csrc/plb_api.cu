@@ -157,28 +157,18 @@ int plb_build(const plb_csr* g, const int32_t* vertex_order, const plb_options* 
     return plb::build_core(g->row_ptr, g->col, vertex_order, g->n, g->nnz, o, s, out);
 }
 
-int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k, const plb_options* opt,
-                    plb_stream stream, plb_labels** outs) {
-    if (k < 0 || (k > 0 && (!gs || !orders || !outs))) return PLB_ERR_INVALID;
-    if (k == 0) return PLB_OK;
-    if (k > (1 << 24)) return PLB_ERR_TOO_LARGE;
-    plb_options o;
-    if (opt) o = *opt; else plb_default_options(&o);
-    if (!sane_options(o)) return PLB_ERR_INVALID;
-    cudaStream_t s = (cudaStream_t)stream;
-    (void)cudaGetLastError();
+// One round loop over the disjoint union of parts [0, k) of gs/orders.
+static int build_union(const plb_csr* gs, const int32_t* const* orders, int64_t k, const plb_options& o,
+                       cudaStream_t s, plb_labels** outs) {
     std::vector<plb::GraphDesc> hd((size_t)k);
     std::vector<int64_t> vb((size_t)k + 1), eb((size_t)k + 1);
     int64_t N = 0, E = 0;
     for (int64_t i = 0; i < k; ++i) {
-        const int c = check_csr(&gs[i], orders[i]);
-        if (c != PLB_OK) return c;
         vb[i] = N;
         eb[i] = E;
         hd[i] = {gs[i].row_ptr, gs[i].col, orders[i], N, E, gs[i].n, gs[i].nnz};
         N += gs[i].n;
         E += gs[i].nnz;
-        if (N >= PLB_MAX_VERTICES) return PLB_ERR_TOO_LARGE;
     }
     vb[k] = N;
     eb[k] = E;
@@ -268,6 +258,39 @@ int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k, 
     delete U;
     cleanup();
     cudaStreamSynchronize(s);
+    return PLB_OK;
+}
+
+int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k, const plb_options* opt,
+                    plb_stream stream, plb_labels** outs) {
+    if (k < 0 || (k > 0 && (!gs || !orders || !outs))) return PLB_ERR_INVALID;
+    if (k == 0) return PLB_OK;
+    if (k > (1 << 24)) return PLB_ERR_TOO_LARGE;
+    plb_options o;
+    if (opt) o = *opt; else plb_default_options(&o);
+    if (!sane_options(o)) return PLB_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    for (int64_t i = 0; i < k; ++i) {
+        const int c = check_csr(&gs[i], orders[i]);
+        if (c != PLB_OK) return c;
+    }
+    // consecutive groups of parts whose union stays below 2^24 vertices; one
+    // round loop per group
+    int64_t lo = 0;
+    while (lo < k) {
+        int64_t hi = lo, nsum = 0;
+        while (hi < k && nsum + gs[hi].n < PLB_MAX_VERTICES) nsum += gs[hi++].n;
+        const int st = build_union(gs + lo, orders + lo, hi - lo, o, s, outs + lo);
+        if (st != PLB_OK) {
+            for (int64_t i = 0; i < lo; ++i) {
+                plb_labels_free(outs[i]);
+                outs[i] = nullptr;
+            }
+            return st;
+        }
+        lo = hi;
+    }
     return PLB_OK;
 }
 
