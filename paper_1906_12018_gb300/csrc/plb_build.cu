@@ -193,7 +193,6 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int32_t* A = pool.alloc<int32_t>(n);
     int32_t* R = pool.alloc<int32_t>(n);
     int32_t* O1 = pool.alloc<int32_t>(n);
-    int32_t* O2 = pool.alloc<int32_t>(n);
     int64_t* aoff = pool.alloc<int64_t>(n + 1);
     PLB_ALLOC_OK();
     PLB_CK(cudaMemsetAsync(recv, 0, sizeof(unsigned long long) * std::max<int64_t>(n, 1), s));
@@ -245,8 +244,6 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     lim.warp_bound = 2 * (int64_t)warp_cand;
     lim.warp_label = warp_label;
     lim.warp_deg = (int64_t)32 * 64;
-    lim.block_cand = block_cand;
-    lim.block_label = ((int64_t(1) << b_log_m) - 2 * bthr) / 2;
     if (w_smem > 227 * 1024 || b_smem > 227 * 1024) return PLB_ERR_INVALID;
     PLB_CK(cudaFuncSetAttribute(k_gp_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w_smem));
     PLB_CK(cudaFuncSetAttribute(k_gp_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_smem));
@@ -255,9 +252,9 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_gp_block, bthr, b_smem);
     const int grid_w = sms * std::max(1, occ_w);
     const int grid_b = sms * std::max(1, occ_b);
-    uint32_t* gscratch = nullptr;
-    int64_t gwords = 0;
-    const int g_blocks = 16;
+    // block tier: per-block buffer of accepted hubs (at most v < n per vertex)
+    uint32_t* gacc = pool.alloc<uint32_t>((int64_t)grid_b * std::max<int64_t>(n, 1));
+    PLB_ALLOC_OK();
 
     // ------------------------------------------------------------ rounds
     int status = PLB_OK;
@@ -271,7 +268,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         k_active_degree<<<gflat, kFlatThreads, 0, s>>>(roff, A, ctr, tmp64, n);
         PLB_CK(exclusive_scan_i64(tmp64, aoff, n, scan_scr, s));
         k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[cur], fhub[cur], A, aoff, ctr, recv, n);
-        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse[nxt], R, O1, O2, ctr, lim);
+        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse[nxt], R, O1, ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(ctr);
         PLB_CK(cudaGetLastError());
         st.launches += 5;
@@ -319,17 +316,18 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             p.log_s = w_log_s;
             p.log_m = w_log_m;
             p.cand_limit = warp_cand;
-            p.label_limit = warp_label;
             k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
             cudaEvent_t g1 = tm.on ? tm.mark() : nullptr;
-            // block tier
+            // block tier (never escalates)
             p.list = O1;
             p.list_n = &ctr->nO1;
-            p.esc = O2;
-            p.esc_n = &ctr->nO2;
+            p.esc = nullptr;
+            p.esc_n = nullptr;
             p.log_s = b_log_s;
             p.log_m = b_log_m;
             p.cand_limit = block_cand;
+            p.gscratch = gacc;
+            p.gscratch_words = std::max<int64_t>(n, 1);
             k_gp_block<<<grid_b, bthr, b_smem, s>>>(p);
             cudaEvent_t g2 = tm.on ? tm.mark() : nullptr;
             PLB_CK(cudaGetLastError());
@@ -340,29 +338,6 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             }
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));
-            if (hctr->nO2 > 0) {
-                cudaEvent_t q0 = tm.on ? tm.mark() : nullptr;
-                // global tier: tables in global scratch, sized for any vertex
-                if (!gscratch) {
-                    const int64_t big = (int64_t)pow2_at_least(2 * n + 2 * bthr);
-                    gwords = 2 * big + pow2_at_least(n + 1);
-                    gscratch = pool.alloc<uint32_t>(gwords * g_blocks);
-                    PLB_ALLOC_OK();
-                }
-                p.list = O2;
-                p.list_n = &ctr->nO2;
-                p.esc = O2;
-                p.esc_n = &ctr->nO2;
-                p.gscratch = gscratch;
-                p.gscratch_words = gwords;
-                k_gp_global<<<g_blocks, bthr, 0, s>>>(p);
-                cudaEvent_t q1 = tm.on ? tm.mark() : nullptr;
-                PLB_CK(cudaGetLastError());
-                st.launches += 1;
-                if (tm.on) tm.span(T_GPG, q0, q1);
-                PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
-                PLB_CK(cudaStreamSynchronize(s));
-            }
             if (!hctr->fovf) break;
             // new-frontier buffer too small: grow it and run the gather again
             const int64_t need = (int64_t)hctr->cursor;

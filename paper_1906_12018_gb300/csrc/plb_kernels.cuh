@@ -47,10 +47,9 @@ struct GpParams {
     int* esc_n;
     RoundCounters* ctr;
     uint32_t d;                // round = distance of accepted labels
-    int log_s, log_m;          // warp/block tier table sizes (log2 slots)
-    int cand_limit;            // max unique candidates (power of two)
-    int label_limit;           // max |L(v)| (block tier: escalate beyond)
-    uint32_t* gscratch;        // global tier: per-block table storage
+    int log_s, log_m;          // table sizes (log2 slots): candidate set, L(v) map (block tier: largest)
+    int cand_limit;            // max unique candidates per pass (power of two)
+    uint32_t* gscratch;        // block tier: per-block buffer of accepted hubs
     int64_t gscratch_words;    // words per block
     const int64_t* hoff;       // probe index of L: per row a hub-keyed table (empty rows: none)
     const uint32_t* htab;
@@ -64,8 +63,6 @@ struct TierLimits {
     int64_t warp_bound;   // candidate bound up to which the warp tier is tried
     int64_t warp_label;   // largest |L(v)| of the warp tier
     int64_t warp_deg;     // largest degree of the warp tier
-    int64_t block_cand;   // candidate bound up to which the block tier is used
-    int64_t block_label;  // largest |L(v)| of the block tier
 };
 
 struct WarpSync {

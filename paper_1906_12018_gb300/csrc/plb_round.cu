@@ -171,11 +171,10 @@ __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t*
 }
 
 // Receivers (recv[v] > 0) are routed by the candidate bound min(v, recv[v]),
-// |L(v)| and degree: warp tier (R), block tier (O1) or global tier (O2).
+// |L(v)| and degree: warp tier (R) or block tier (O1).
 // Also clears recv and the new frontier descriptors, and sums the bounds.
 __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const int64_t* loff, int64_t n,
-                          uint64_t* fse_new, int32_t* R, int32_t* O1, int32_t* O2, RoundCounters* ctr,
-                          TierLimits lim) {
+                          uint64_t* fse_new, int32_t* R, int32_t* O1, RoundCounters* ctr, TierLimits lim) {
     unsigned long long bsum = 0;
     const int lane = lane_id();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -188,15 +187,13 @@ __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const i
             bsum += bound;
             const int64_t ll = loff[v + 1] - loff[v];
             const int64_t deg = roff[v + 1] - roff[v];
-            if ((int64_t)bound <= lim.warp_bound && ll <= lim.warp_label && deg <= lim.warp_deg) tier = 0;
-            else if (ll <= lim.block_label) tier = 1;
-            else tier = 2;
+            tier = ((int64_t)bound <= lim.warp_bound && ll <= lim.warp_label && deg <= lim.warp_deg) ? 0 : 1;
         }
         const unsigned am = __activemask();
-        int32_t* lists[3] = {R, O1, O2};
-        int* counts[3] = {&ctr->nR, &ctr->nO1, &ctr->nO2};
+        int32_t* lists[2] = {R, O1};
+        int* counts[2] = {&ctr->nR, &ctr->nO1};
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
+        for (int t = 0; t < 2; ++t) {
             const unsigned m = __ballot_sync(am, tier == t);
             if (m) {
                 const int leader = __ffs(m) - 1;
@@ -233,12 +230,20 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
 }
 
 // ------------------------------------------------------- gather + prune
+// Distance of hub w in the sorted label row r[0..len), or kEmpty.
+__device__ __forceinline__ uint32_t row_find(const uint32_t* r, int64_t len, uint32_t w) {
+    const int64_t i = lower_bound_u32(r, len, pack(w, 0));
+    if (i < len && hub_of(r[i]) == w) return dist_of(r[i]);
+    return kEmpty;
+}
+
 // Distance check of up to 32 candidates held one per lane (valid lanes).
 // A witness for candidate h is a hub w of both v and h with
 // d(w,v) + d(w,h) <= d (the test of Alg. 3 with the labels of round d-1).
 // Each candidate scans the shorter side:
 //   A: the entries of L(h) (its last entry, (h,0), is never a witness and is
-//      skipped), each probed in the shared-memory map M of L(v);
+//      skipped), each looked up in L(v): in the shared-memory map M, or by
+//      binary search in the row lv when M is null;
 //   B: the entries of L(v) with hub < h (only those can be hubs of h), each
 //      probed in h's row of the global probe index (rows of >= 16 entries).
 // All (candidate, entry) pairs are spread over the lanes; a candidate's
@@ -258,7 +263,7 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
         const int64_t x0 = p.hoff[h], x1 = p.hoff[h + 1];
         if (x1 > x0) {
             const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
-            if (2 * lb < la) {
+            if (2 * lb < la || M == nullptr) {
                 items = lb;
                 base = x0;
                 meta = __ffs((int)(x1 - x0));  // log2 + 1
@@ -284,7 +289,7 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
             bool hit = false;
             if (mk == 0) {
                 const uint32_t x = p.lent[bk + j];
-                const uint32_t dv = map_find(M, log_m, hub_of(x));
+                const uint32_t dv = M ? map_find(M, log_m, hub_of(x)) : row_find(lv, lvlen, hub_of(x));
                 hit = dv != kEmpty && dv + dist_of(x) <= p.d;
             } else {
                 const uint32_t y = lv[j];
@@ -301,13 +306,15 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
     return vmask & ~pm;
 }
 
-// Gather of v's messages into the set S: for every neighbour a and every h in
-// dL_{d-1}(a) with h < v and h not already a hub of v (not in M).  Warp-level
-// load-balanced expansion over 32 neighbours at a time.  Stops (returns
-// false) when the set would exceed `limit` entries.
-__device__ __forceinline__ bool gather_warp(const GpParams& p, int32_t v, int64_t nb, int64_t ne, int64_t stride,
-                                            uint32_t* S, int log_s, const uint32_t* M, int log_m, int limit,
-                                            int* cnt_sm, volatile int* ovf_sm, unsigned long long& msgs) {
+// Gather of v's messages with hub in [lo, hi) (hi <= v: only hubs that
+// outrank v) into the set S: the frontier rows dL_{d-1}(a) of the neighbours
+// are sorted, so each row's sub-range is found by binary search.  Warp-level
+// load-balanced expansion over 32 neighbours at a time.  With M, hubs already
+// in L(v) are skipped.  Stops (returns false) when the set would exceed
+// `limit` entries.
+__device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int64_t ne, int64_t stride, uint32_t lo,
+                                             uint32_t hi, uint32_t* S, int log_s, const uint32_t* M, int log_m,
+                                             int limit, int* cnt_sm, volatile int* ovf_sm, unsigned long long& msgs) {
     const int lane = threadIdx.x & 31;
     for (int64_t base = nb; base < ne; base += stride) {
         const int64_t j = base + lane;
@@ -315,8 +322,14 @@ __device__ __forceinline__ bool gather_warp(const GpParams& p, int32_t v, int64_
         int64_t st = 0;
         if (j < ne) {
             const uint64_t f = p.fse[p.rcol[j]];
-            st = (int64_t)fstart(f);
-            c = (int)fcount(f);
+            const uint32_t n0 = fcount(f);
+            if (n0) {
+                const uint32_t* row = p.fhub + fstart(f);
+                const int64_t a0 = lo ? lower_bound_u32(row, n0, lo) : 0;
+                const int64_t a1 = lower_bound_u32(row, n0, hi);
+                st = (int64_t)fstart(f) + a0;
+                c = (int)(a1 - a0);
+            }
         }
         const int incl = warp_incl_scan(c, lane);
         const int total = __shfl_sync(kFull, incl, 31);
@@ -329,7 +342,7 @@ __device__ __forceinline__ bool gather_warp(const GpParams& p, int32_t v, int64_
             const int exk = __shfl_sync(kFull, excl, k);
             if (it < total) {
                 const uint32_t h = p.fhub[stk + (it - exk)];
-                if (h < (uint32_t)v && map_find(M, log_m, h) == kEmpty) {
+                if (!M || map_find(M, log_m, h) == kEmpty) {
                     if (*(volatile int*)cnt_sm >= limit) {
                         *ovf_sm = 1;
                     } else if (set_insert(S, log_s, h)) {
@@ -374,8 +387,8 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
         for (int64_t j = lane; j < ll; j += 32) map_insert(M, p.log_m, p.lent[lb + j]);
         __syncwarp();
         const int64_t nb = p.roff[v], ne = p.roff[v + 1];
-        const bool ok = gather_warp(p, v, nb, ne, 32, S, p.log_s, M, p.log_m, p.cand_limit, &wsc[0],
-                                    (volatile int*)&wsc[1], c_msgs);
+        const bool ok = gather_range(p, nb, ne, 32, 0u, (uint32_t)v, S, p.log_s, M, p.log_m, p.cand_limit, &wsc[0],
+                                     (volatile int*)&wsc[1], c_msgs);
         __syncwarp();
         const int nS = *(volatile int*)&wsc[0];
         if (!ok || nS > p.cand_limit) {
@@ -444,127 +457,133 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
 }
 
 // Block-per-vertex scalars in shared memory (ints)
-enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_BOUND = 4 /* 2 ints */, SH_START = 6 /* 2 ints */,
+enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_START = 6 /* 2 ints */,
        SH_PM = 16 /* one word per warp */, SH_WORDS = 48 };
 
-// One block per vertex; tables either in shared memory (kGlobal = false) or
-// in this block's slice of global scratch sized for the vertex (kGlobal).
-template <bool kGlobal>
-__device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* tabs, int log_s_max, int log_m_max,
-                                int* sh, unsigned long long* cnt) {
+// One block per vertex, any size.  The candidates are processed in passes
+// over hub ranges [lo, hi): each pass gathers the messages of its range into
+// the shared-memory set (a pass whose set overflows is retried on half the
+// range), checks them and appends the sorted survivors to this block's
+// global scratch; passes run in increasing hub order, so the concatenation
+// is sorted.  L(v) is staged into the shared-memory map when it fits;
+// otherwise membership in L(v) is a binary search in its row.
+__device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
+                                uint32_t* gacc, int* sh, unsigned long long* cnt) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
     const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
     const int64_t nb = p.roff[v], ne = p.roff[v + 1];
+    const uint32_t* lv = p.lent + lb;
+    const int log_s = p.log_s, S_CAP = 1 << log_s, limit = p.cand_limit;
     int log_m = ceil_log2_i64(2 * ll + 2 * nthr);
     if (log_m < 5) log_m = 5;
-    int log_s = log_s_max, cap = p.cand_limit;
-    if (kGlobal) {
-        // bound on unique candidates: min(v, sum of frontier sizes of the neighbours)
-        int64_t part = 0;
-        for (int64_t j = nb + tid; j < ne; j += nthr) part += fcount(p.fse[p.rcol[j]]);
-        part = warp_sum(part);
-        if (lane == 0) atomicAdd((unsigned long long*)(sh + SH_BOUND), (unsigned long long)part);
+    const bool useM = log_m <= p.log_m;
+    const uint32_t* Mp = useM ? M : nullptr;
+    if (useM) {
+        for (int s = tid; s < (1 << log_m); s += nthr) M[s] = kEmpty;
         __syncthreads();
-        int64_t bound = (int64_t)(*(volatile unsigned long long*)(sh + SH_BOUND));
-        if (bound > v) bound = v;
-        log_s = ceil_log2_i64(2 * bound + 2 * nthr);
-        if (log_s < 5) log_s = 5;
-        cap = 1 << ceil_log2_i64(bound + 1);
-        __syncthreads();
-        if (tid == 0) *(unsigned long long*)(sh + SH_BOUND) = 0;
-    } else if (log_m > log_m_max) {
-        if (tid == 0) {
-            const int o = atomicAdd(p.esc_n, 1);
-            p.esc[o] = v;
-        }
-        return;
-    }
-    const int S_CAP = 1 << log_s, M_CAP = 1 << log_m;
-    uint32_t* S = tabs;
-    uint32_t* M = S + S_CAP;
-    uint32_t* C = M + M_CAP;
-    for (int s = tid; s < S_CAP; s += nthr) S[s] = kEmpty;
-    for (int s = tid; s < M_CAP; s += nthr) M[s] = kEmpty;
-    if (tid == 0) {
-        sh[SH_UNIQ] = 0;
-        sh[SH_OVF] = 0;
-        sh[SH_ACC] = 0;
-        sh[SH_NC] = 0;
-    }
-    __syncthreads();
-    for (int64_t j = tid; j < ll; j += nthr) map_insert(M, log_m, p.lent[lb + j]);
-    __syncthreads();
-    // gather: warp w handles neighbour chunks w, w + nw, ...
-    gather_warp(p, v, nb + 32 * wid, ne, 32 * nw, S, log_s, M, log_m, cap, &sh[SH_UNIQ],
-                (volatile int*)&sh[SH_OVF], cnt[1]);
-    __syncthreads();
-    const int nS = *(volatile int*)&sh[SH_UNIQ];
-    if (*(volatile int*)&sh[SH_OVF] || nS > cap) {
-        __syncthreads();
-        if (tid == 0) {
-            const int o = atomicAdd(p.esc_n, 1);
-            p.esc[o] = v;
-        }
-        return;
+        for (int64_t j = tid; j < ll; j += nthr) map_insert(M, log_m, lv[j]);
     }
     if (tid == 0) {
         cnt[0] += ne - nb;
-        cnt[2] += nS;
         cnt[3] += ll;
         cnt[6] += 1;
     }
-    // compact the set into C (any order)
-    for (int sb = 32 * wid; sb < S_CAP; sb += 32 * nw) {
-        const uint32_t h = S[sb + lane];
-        const bool has = h != kEmpty;
-        const unsigned m = __ballot_sync(kFull, has);
-        int base = 0;
-        if (lane == 0 && m) base = atomicAdd(&sh[SH_NC], __popc(m));
-        base = __shfl_sync(kFull, base, 0);
-        if (has) C[base + __popc(m & ((1u << lane) - 1u))] = h;
-    }
-    __syncthreads();
-    const int nc = *(volatile int*)&sh[SH_NC];
-    // distance checks: warp w takes candidate chunks w, w + nw, ...; the
-    // accepted hubs are appended to A (the set's storage, free by now)
-    uint32_t* Acc = S;
-    for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
-        const bool valid = cb + lane < nc;
-        const uint32_t h = valid ? C[cb + lane] : 0u;
-        const unsigned okm = check_chunk(p, M, log_m, p.lent + lb, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4]);
-        int base = 0;
-        if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
-        base = __shfl_sync(kFull, base, 0);
-        if ((okm >> lane) & 1u) Acc[base + __popc(okm & ((1u << lane) - 1u))] = h;
-    }
-    __syncthreads();
-    const int nacc = *(volatile int*)&sh[SH_ACC];
-    if (nacc > 0) {
-        int P = 1;
-        while (P < nacc) P <<= 1;
-        for (int s = nacc + tid; s < P; s += nthr) Acc[s] = kEmpty;
-        __syncthreads();
-        group_bitonic_sort(Acc, P, tid, nthr, BlockSync());
-        C = Acc;
+    int64_t total_acc = 0;
+    uint32_t lo = 0;
+    int64_t width = v;
+    while ((int64_t)lo < (int64_t)v) {
+        const uint32_t hi = (uint32_t)min((int64_t)v, (int64_t)lo + width);
+        for (int s = tid; s < S_CAP; s += nthr) S[s] = kEmpty;
         if (tid == 0) {
-            const unsigned long long start = atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
+            sh[SH_UNIQ] = 0;
+            sh[SH_OVF] = 0;
+            sh[SH_ACC] = 0;
+            sh[SH_NC] = 0;
+        }
+        __syncthreads();
+        gather_range(p, nb + 32 * wid, ne, 32 * nw, lo, hi, S, log_s, Mp, log_m, limit, &sh[SH_UNIQ],
+                     (volatile int*)&sh[SH_OVF], cnt[1]);
+        __syncthreads();
+        const int nS = *(volatile int*)&sh[SH_UNIQ];
+        if (*(volatile int*)&sh[SH_OVF] || nS > limit) {
+            width = (int64_t)(hi - lo) / 2;
+            if (width < 1) width = 1;
+            __syncthreads();
+            continue;
+        }
+        // compact the set into C (any order)
+        for (int sb = 32 * wid; sb < S_CAP; sb += 32 * nw) {
+            const uint32_t h = S[sb + lane];
+            const bool has = h != kEmpty;
+            const unsigned m = __ballot_sync(kFull, has);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&sh[SH_NC], __popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (has) C[base + __popc(m & ((1u << lane) - 1u))] = h;
+        }
+        __syncthreads();
+        const int nc = *(volatile int*)&sh[SH_NC];
+        if (tid == 0) cnt[2] += nc;
+        // distance checks: warp w takes candidate chunks w, w + nw, ...; the
+        // survivors are appended to Acc (the set's storage, free by now)
+        uint32_t* Acc = S;
+        for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
+            bool valid = cb + lane < nc;
+            const uint32_t h = valid ? C[cb + lane] : 0u;
+            if (!useM && valid && row_find(lv, ll, h) != kEmpty) valid = false;  // already a hub of v
+            const unsigned okm = check_chunk(p, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4]);
+            int base = 0;
+            if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
+            base = __shfl_sync(kFull, base, 0);
+            if ((okm >> lane) & 1u) Acc[base + __popc(okm & ((1u << lane) - 1u))] = h;
+        }
+        __syncthreads();
+        const int nacc = *(volatile int*)&sh[SH_ACC];
+        if (nacc > 0) {
+            int P = 1;
+            while (P < nacc) P <<= 1;
+            for (int s = nacc + tid; s < P; s += nthr) Acc[s] = kEmpty;
+            __syncthreads();
+            group_bitonic_sort(Acc, P, tid, nthr, BlockSync());
+            for (int j = tid; j < nacc; j += nthr) gacc[total_acc + j] = Acc[j];
+            total_acc += nacc;
+        }
+        __syncthreads();
+        width = 2 * (int64_t)(hi - lo);
+        lo = hi;
+    }
+    if (total_acc > 0) {
+        if (tid == 0) {
+            const unsigned long long start = atomicAdd(&p.ctr->cursor, (unsigned long long)total_acc);
             *(unsigned long long*)(sh + SH_START) = start;
         }
         __syncthreads();
         const unsigned long long start = *(volatile unsigned long long*)(sh + SH_START);
-        if (start + nacc <= p.fcap) {
-            for (int j = tid; j < nacc; j += nthr) p.fhub_new[start + j] = C[j];
-            if (tid == 0) p.fse_new[v] = fpack(start, (uint32_t)nacc);
+        if (start + total_acc <= p.fcap) {
+            for (int64_t j = tid; j < total_acc; j += nthr) p.fhub_new[start + j] = gacc[j];
+            if (tid == 0) p.fse_new[v] = fpack(start, (uint32_t)total_acc);
         } else if (tid == 0) {
             p.ctr->fovf = 1;
         }
-        if (tid == 0) cnt[5] += nacc;
+        if (tid == 0) cnt[5] += total_acc;
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ void flush_block_counters(const GpParams& p, unsigned long long* cnt, int tier) {
+__global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
+    extern __shared__ uint32_t sm[];
+    int* sh = reinterpret_cast<int*>(sm);
+    uint32_t* S = sm + SH_WORDS;
+    uint32_t* M = S + (1 << p.log_s);
+    uint32_t* C = M + (1 << p.log_m);
+    uint32_t* gacc = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
+    unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+    const int n1 = *p.list_n;
+    for (int i = blockIdx.x; i < n1; i += gridDim.x) {
+        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, cnt);
+        __syncthreads();
+    }
     cnt[1] = warp_sum(cnt[1]);
     cnt[4] = warp_sum(cnt[4]);
     if ((threadIdx.x & 31) == 0) {
@@ -576,35 +595,8 @@ __device__ __forceinline__ void flush_block_counters(const GpParams& p, unsigned
         atomicAdd(&p.ctr->uniq, cnt[2]);
         atomicAdd(&p.ctr->staged, cnt[3]);
         atomicAdd(&p.ctr->accepted, cnt[5]);
-        atomicAdd(&p.ctr->tier[tier], cnt[6]);
+        atomicAdd(&p.ctr->tier[1], cnt[6]);
     }
-}
-
-__global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
-    extern __shared__ uint32_t sm[];
-    int* sh = reinterpret_cast<int*>(sm);
-    uint32_t* tabs = sm + SH_WORDS;
-    unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
-    const int n1 = *p.list_n;
-    for (int i = blockIdx.x; i < n1; i += gridDim.x) {
-        gp_block_vertex<false>(p, p.list[i], tabs, p.log_s, p.log_m, sh, cnt);
-        __syncthreads();
-    }
-    flush_block_counters(p, cnt, 1);
-}
-
-__global__ void __launch_bounds__(512) k_gp_global(GpParams p) {
-    __shared__ __align__(8) int sh[SH_WORDS];
-    unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
-    const int n2 = *p.list_n;
-    uint32_t* tabs = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
-    if (threadIdx.x == 0) *(unsigned long long*)(sh + SH_BOUND) = 0;
-    __syncthreads();
-    for (int i = blockIdx.x; i < n2; i += gridDim.x) {
-        gp_block_vertex<true>(p, p.list[i], tabs, 0, 0, sh, cnt);
-        __syncthreads();
-    }
-    flush_block_counters(p, cnt, 2);
 }
 
 // ------------------------------------------------------------ probe index
