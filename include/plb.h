@@ -107,7 +107,8 @@ typedef struct {
     int64_t receivers[PLB_MAX_ROUNDS];   /* vertices that gathered messages */
     int64_t accepted[PLB_MAX_ROUNDS];    /* new labels (|dL_d|) */
     int64_t unique_round[PLB_MAX_ROUNDS];  /* distinct candidates checked in round d */
-    int64_t probed_round[PLB_MAX_ROUNDS];  /* L(h) entries probed in round d */
+    int64_t probed_round[PLB_MAX_ROUNDS];  /* label entries probed in distance checks in round d */
+    int64_t prefiltered_round[PLB_MAX_ROUNDS]; /* candidates pruned by the top-hub witness prefilter */
     int64_t messages_round[PLB_MAX_ROUNDS];/* frontier hubs read by the gather in round d */
     double ms_round[PLB_MAX_ROUNDS];       /* device ms of round d (profile = 1 only) */
     /* totals over rounds */

@@ -201,6 +201,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     st.launches += 1;
     int64_t T = n;  // labels so far
     int cur = 0;    // index of current L and previous frontier
+    // top-hub distance rows (witness prefilter), updated by each merge
+    uint8_t* top = pool.alloc<uint8_t>(n * kTopHubs);
+    PLB_ALLOC_OK();
+    k_top_init<<<flat_grid_cap, kFlatThreads, 0, s>>>(top, n);
     // probe index of L (hub-keyed table per long row), rebuilt after each merge
     int64_t* hoff = pool.alloc<int64_t>(n + 1);
     int64_t hcap = std::max<int64_t>(4 * n, 1024);
@@ -303,6 +307,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             p.d = (uint32_t)d;
             p.hoff = hoff;
             p.htab = htab;
+            p.top = top;
             if (rerun) {
                 k_rerun_reset<<<gflat, kFlatThreads, 0, s>>>(ctr, fse[nxt], n);
                 st.launches += 1;
@@ -353,6 +358,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             st.receivers[d] = (int64_t)hctr->nR + hctr->nO1_base + hctr->nO2_base;
             st.accepted[d] = acc;
             st.unique_round[d] = (int64_t)hctr->uniq;
+            st.prefiltered_round[d] = (int64_t)hctr->prefiltered;
             st.probed_round[d] = (int64_t)hctr->probed;
             st.messages_round[d] = (int64_t)hctr->msgs;
             if (tm.on) round_ev.push_back({d, r0});
@@ -382,7 +388,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         k_merge_old<<<grid_for((T + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(
             loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], n);
         k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
-            loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], A, ctr, (uint32_t)d);
+            loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], A, ctr, (uint32_t)d, top);
         PLB_CK(cudaGetLastError());
         st.launches += 5;
         T = Tn;

@@ -24,6 +24,7 @@ struct RoundCounters {
     unsigned long long arcs, msgs, uniq, staged, probed;
     unsigned long long tier[3];
     unsigned long long bound_sum; // sum over receivers of the candidate bound min(v, messages)
+    unsigned long long prefiltered; // candidates pruned by the top-hub witness prefilter
     int nR, nO1, nO2;             // receivers: warp tier, block tier, global tier
     int nA;                       // next active list (kept across the per-round reset)
     int nO1_base, nO2_base;       // tier-list sizes made by k_collect (for reruns)
@@ -53,7 +54,13 @@ struct GpParams {
     int64_t gscratch_words;    // words per block
     const int64_t* hoff;       // probe index of L: per row a hub-keyed table (empty rows: none)
     const uint32_t* htab;
+    const uint8_t* top;        // per vertex: d(w, x) for the kTopHubs highest-ranked hubs w (255: not a hub)
 };
+
+// Witness prefilter: every vertex keeps the label distances of the top-ranked
+// kTopHubs hubs as a byte row, so the label test restricted to those hubs is
+// a handful of byte-SIMD operations (exact: a hit is a real witness).
+constexpr int kTopHubs = 256;
 
 // Rows of L with at least this many entries get a hub-keyed probe table.
 constexpr int kIndexMinLen = 16;

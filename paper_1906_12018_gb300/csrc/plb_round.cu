@@ -306,6 +306,28 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
     return vmask & ~pm;
 }
 
+// Top-hub witness prefilter for the 32 candidates of a chunk (one per lane):
+// candidate h has a witness among the kTopHubs highest-ranked hubs iff some
+// byte position w has top[v][w] + top[h][w] <= d (saturating byte add; 255 =
+// not a hub).  Each lane holds 8 bytes of v's row (tv0, tv1); the warp tests
+// one candidate per step with one coalesced 256-byte load.  Returns the mask
+// of lanes whose candidate is pruned.
+__device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, uint32_t tv0, uint32_t tv1, uint32_t d,
+                                                  uint32_t h, bool valid) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t dd = d * 0x01010101u;
+    unsigned todo = __ballot_sync(kFull, valid), pruned = 0;
+    while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t hk = __shfl_sync(kFull, h, k);
+        const uint2 th = *reinterpret_cast<const uint2*>(top + (int64_t)hk * kTopHubs + 8 * lane);
+        const uint32_t hit = __vcmpleu4(__vaddus4(th.x, tv0), dd) | __vcmpleu4(__vaddus4(th.y, tv1), dd);
+        if (__any_sync(kFull, hit != 0)) pruned |= 1u << k;
+    }
+    return pruned;
+}
+
 // Gather of v's messages with hub in [lo, hi) (hi <= v: only hubs that
 // outrank v) into the set S: the frontier rows dL_{d-1}(a) of the neighbours
 // are sorted, so each row's sub-range is found by binary search.  Warp-level
@@ -372,6 +394,7 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
     uint32_t* M = S + S_CAP;
     uint32_t* C = M + M_CAP;
     unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
+    unsigned long long c_pref = 0;
     const int nlist = *p.list_n;
     for (int i = blockIdx.x * nwarps + wib; i < nlist; i += gridDim.x * nwarps) {
         __syncwarp();
@@ -415,11 +438,15 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
         }
         __syncwarp();
         // distance checks, 32 candidates at a time; survivors compacted in place
+        const uint2 tv = *reinterpret_cast<const uint2*>(p.top + (int64_t)v * kTopHubs + 8 * lane);
         int nacc = 0;
         for (int cb = 0; cb < nc; cb += 32) {
-            const bool valid = cb + lane < nc;
+            bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
             __syncwarp();
+            const unsigned pf = top_prefilter(p.top, tv.x, tv.y, p.d, h, valid);
+            if (lane == 0) c_pref += __popc(pf);
+            valid = valid && !((pf >> lane) & 1u);
             const unsigned okm = check_chunk(p, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3], c_probed);
             if ((okm >> lane) & 1u) C[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
@@ -453,6 +480,7 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
         atomicAdd(&p.ctr->probed, c_probed);
         atomicAdd(&p.ctr->accepted, c_acc);
         atomicAdd(&p.ctr->tier[0], c_vert);
+        atomicAdd(&p.ctr->prefiltered, c_pref);
     }
 }
 
@@ -489,6 +517,7 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
         cnt[3] += ll;
         cnt[6] += 1;
     }
+    const uint2 tv = *reinterpret_cast<const uint2*>(p.top + (int64_t)v * kTopHubs + 8 * lane);
     int64_t total_acc = 0;
     uint32_t lo = 0;
     int64_t width = v;
@@ -532,6 +561,9 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
             bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
             if (!useM && valid && row_find(lv, ll, h) != kEmpty) valid = false;  // already a hub of v
+            const unsigned pf = top_prefilter(p.top, tv.x, tv.y, p.d, h, valid);
+            if (lane == 0) cnt[7] += __popc(pf);
+            valid = valid && !((pf >> lane) & 1u);
             const unsigned okm = check_chunk(p, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4]);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
@@ -578,7 +610,7 @@ __global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
     uint32_t* M = S + (1 << p.log_s);
     uint32_t* C = M + (1 << p.log_m);
     uint32_t* gacc = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
-    unsigned long long cnt[7] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int n1 = *p.list_n;
     for (int i = blockIdx.x; i < n1; i += gridDim.x) {
         gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, cnt);
@@ -589,6 +621,7 @@ __global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&p.ctr->msgs, cnt[1]);
         atomicAdd(&p.ctr->probed, cnt[4]);
+        atomicAdd(&p.ctr->prefiltered, cnt[7]);
     }
     if (threadIdx.x == 0) {
         atomicAdd(&p.ctr->arcs, cnt[0]);
@@ -684,7 +717,7 @@ __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int
 // New entries (dist d) of each active vertex: warp per vertex.
 __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
                             const uint64_t* fse_new, const uint32_t* fhub_new, const int32_t* A,
-                            const RoundCounters* ctr, uint32_t d) {
+                            const RoundCounters* ctr, uint32_t d, uint8_t* top) {
     const int nA = ctr->nA;
     const int lane = lane_id();
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -698,7 +731,19 @@ __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int
             const uint32_t h = fr[j];
             const int64_t pos = loff_new[v] + j + lower_bound_u32(lent + ob, ol, pack(h, 0));
             lent_new[pos] = pack(h, d);
+            if (h < (uint32_t)kTopHubs) top[(int64_t)v * kTopHubs + h] = (uint8_t)d;
         }
+    }
+}
+
+// top[x][w] = 255 except top[w][w] = 0 for w < kTopHubs (the self labels).
+__global__ void k_top_init(uint8_t* top, int64_t n) {
+    const int64_t words = n * (kTopHubs / 4);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i / (kTopHubs / 4), w0 = (i % (kTopHubs / 4)) * 4;
+        uint32_t word = 0xFFFFFFFFu;
+        if (x >= w0 && x < w0 + 4 && x < kTopHubs) word &= ~(0xFFu << (8 * (x - w0)));
+        reinterpret_cast<uint32_t*>(top)[i] = word;
     }
 }
 

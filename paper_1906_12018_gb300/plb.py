@@ -82,6 +82,7 @@ class BuildStats(ctypes.Structure):
         ("accepted", ctypes.c_int64 * MAX_ROUNDS),
         ("unique_round", ctypes.c_int64 * MAX_ROUNDS),
         ("probed_round", ctypes.c_int64 * MAX_ROUNDS),
+        ("prefiltered_round", ctypes.c_int64 * MAX_ROUNDS),
         ("messages_round", ctypes.c_int64 * MAX_ROUNDS),
         ("ms_round", ctypes.c_double * MAX_ROUNDS),
         ("arcs_scanned", ctypes.c_int64),
@@ -111,6 +112,7 @@ class BuildStats(ctypes.Structure):
             "accepted": list(self.accepted[1 : r + 1]),
             "unique_round": list(self.unique_round[1 : r + 1]),
             "probed_round": list(self.probed_round[1 : r + 1]),
+            "prefiltered_round": list(self.prefiltered_round[1 : r + 1]),
             "messages_round": list(self.messages_round[1 : r + 1]),
             "ms_round": list(self.ms_round[1 : r + 1]),
             "arcs_scanned": self.arcs_scanned,
