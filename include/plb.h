@@ -70,7 +70,7 @@ typedef struct {
 typedef struct {
     int32_t validate;          /* 1: check CSR and order on the device first (default 1) */
     int32_t warp_label_cap;    /* largest |L(v)| handled one-vertex-per-warp (default 512) */
-    int32_t warp_cand_cap;     /* largest unique-candidate count per warp-vertex (default 256) */
+    int32_t warp_cand_cap;     /* largest unique-candidate count per warp-vertex (default 512) */
     int32_t block_label_cap;   /* largest |L(v)| handled one-vertex-per-block in shared memory */
     int32_t block_cand_cap;    /* largest candidate count for the block tier */
     int32_t block_threads;     /* threads of the block tier (multiple of 32, <= 1024) */
@@ -172,6 +172,11 @@ int64_t plb_labels_bytes(const plb_labels* labels);
 
 /* Release a label set (synchronises the device first). NULL is accepted. */
 int plb_labels_free(plb_labels* labels);
+
+/* The library allocates from its own stream-ordered pool per device and keeps
+ * freed blocks for reuse by later builds.  This returns every cached,
+ * currently unused block to the driver (synchronises the device). */
+int plb_release_cached_memory(void);
 
 /* Degree order (Sec. 6.1: vertices ordered by degree): order_out (device,
  * int32[n]) receives rank -> id, degree descending, ties by smaller id.

@@ -108,7 +108,7 @@ void plb_default_options(plb_options* o) {
     *o = plb_options{};
     o->validate = 1;
     o->warp_label_cap = 512;
-    o->warp_cand_cap = 256;
+    o->warp_cand_cap = 512;
     o->block_label_cap = 4096;
     o->block_cand_cap = 4096;
     o->block_threads = 512;
@@ -133,7 +133,7 @@ static bool sane_options(const plb_options& o) {
 
 static int empty_labels(plb_labels** out, cudaStream_t s) {
     plb_labels* L = new plb_labels();
-    if (cudaMallocAsync((void**)&L->off, sizeof(int64_t), s) != cudaSuccess ||
+    if (plb::dev_alloc((void**)&L->off, sizeof(int64_t), s) != cudaSuccess ||
         cudaMemsetAsync(L->off, 0, sizeof(int64_t), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         (void)cudaGetLastError();
         delete L;
@@ -180,13 +180,13 @@ static int build_union(const plb_csr* gs, const int32_t* const* orders, int64_t 
         for (void* p : {(void*)dgd, (void*)dvb, (void*)deb, (void*)U_off, (void*)eoff, (void*)U_col, (void*)U_ord})
             if (p) cudaFreeAsync(p, s);
     };
-    if (cudaMallocAsync((void**)&dgd, sizeof(plb::GraphDesc) * k, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&dvb, sizeof(int64_t) * (k + 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&deb, sizeof(int64_t) * (k + 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&eoff, sizeof(int64_t) * (k + 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&U_off, sizeof(int64_t) * (N + 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&U_col, sizeof(int32_t) * std::max<int64_t>(E, 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&U_ord, sizeof(int32_t) * std::max<int64_t>(N, 1), s) != cudaSuccess) {
+    if (plb::dev_alloc((void**)&dgd, sizeof(plb::GraphDesc) * k, s) != cudaSuccess ||
+        plb::dev_alloc((void**)&dvb, sizeof(int64_t) * (k + 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&deb, sizeof(int64_t) * (k + 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&eoff, sizeof(int64_t) * (k + 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&U_off, sizeof(int64_t) * (N + 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&U_col, sizeof(int32_t) * std::max<int64_t>(E, 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&U_ord, sizeof(int32_t) * std::max<int64_t>(N, 1), s) != cudaSuccess) {
         (void)cudaGetLastError();
         cleanup();
         return PLB_ERR_OOM;
@@ -211,7 +211,7 @@ static int build_union(const plb_csr* gs, const int32_t* const* orders, int64_t 
     }
     // split into per-part label sets sharing the union's storage
     int64_t* off_all = nullptr;
-    if (cudaMallocAsync((void**)&off_all, sizeof(int64_t) * (N + k), s) != cudaSuccess) {
+    if (plb::dev_alloc((void**)&off_all, sizeof(int64_t) * (N + k), s) != cudaSuccess) {
         (void)cudaGetLastError();
         cleanup();
         plb_labels_free(U);

@@ -23,7 +23,7 @@ struct DevPool {
     T* alloc(int64_t count) {
         void* p = nullptr;
         const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
-        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        if (plb::dev_alloc(&p, bytes, s) != cudaSuccess) {
             (void)cudaGetLastError();
             failed = true;
             return nullptr;
@@ -429,11 +429,11 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         delete L;
         return code;
     };
-    if (cudaMallocAsync((void**)&L->off, sizeof(int64_t) * (n + 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&L->packed, sizeof(uint32_t) * std::max<int64_t>(T, 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&L->hub, sizeof(uint32_t) * std::max<int64_t>(T, 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&L->dist, std::max<int64_t>(T, 1), s) != cudaSuccess ||
-        cudaMallocAsync((void**)&L->order, sizeof(int32_t) * std::max<int64_t>(n, 1), s) != cudaSuccess) {
+    if (plb::dev_alloc((void**)&L->off, sizeof(int64_t) * (n + 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&L->packed, sizeof(uint32_t) * std::max<int64_t>(T, 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&L->hub, sizeof(uint32_t) * std::max<int64_t>(T, 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&L->dist, std::max<int64_t>(T, 1), s) != cudaSuccess ||
+        plb::dev_alloc((void**)&L->order, sizeof(int32_t) * std::max<int64_t>(n, 1), s) != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(PLB_ERR_OOM);
     }

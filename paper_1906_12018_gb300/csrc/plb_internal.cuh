@@ -160,6 +160,10 @@ struct plb_labels {
 
 namespace plb {
 
+// Stream-ordered allocation from the library's per-device pool (freed with
+// cudaFreeAsync, or cudaFree after synchronising).
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
+
 // Device-wide exclusive scan of int64 values; out may alias in.
 // count(i) is evaluated for i in [0, n) and out[n] receives the total.
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* block_sums,

@@ -316,7 +316,8 @@ __device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, uint32_t t
                                                   uint32_t h, bool valid) {
     const int lane = threadIdx.x & 31;
     const uint32_t dd = d * 0x01010101u;
-    unsigned todo = __ballot_sync(kFull, valid), pruned = 0;
+    // d <= 254 keeps "absent" (255, saturated) above every threshold
+    unsigned todo = __ballot_sync(kFull, valid && d <= 254u), pruned = 0;
     while (todo) {
         const int k = __ffs(todo) - 1;
         todo &= todo - 1;

@@ -125,7 +125,7 @@ extern "C" int plb_degree_order(const plb_csr* g, int32_t* order_out, plb_stream
     int64_t n2 = 1;
     while (n2 < g->n) n2 <<= 1;
     uint64_t* keys = nullptr;
-    if (cudaMallocAsync((void**)&keys, sizeof(uint64_t) * n2, s) != cudaSuccess) {
+    if (plb::dev_alloc((void**)&keys, sizeof(uint64_t) * n2, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return PLB_ERR_OOM;
     }

@@ -167,6 +167,8 @@ def _lib():
     lib.plb_labels_free.restype = I
     lib.plb_degree_order.argtypes = [ctypes.POINTER(CSR), P, P]
     lib.plb_degree_order.restype = I
+    lib.plb_release_cached_memory.argtypes = []
+    lib.plb_release_cached_memory.restype = I
     lib.plb_degree_order_noalloc.argtypes = [ctypes.POINTER(CSR), P, P]
     lib.plb_degree_order_noalloc.restype = I
     lib.plb_strerror.argtypes = [I]
@@ -180,7 +182,8 @@ def _lib():
 def exported_symbols() -> list[str]:
     """Names of the entry points declared in include/plb.h."""
     return ["plb_default_options", "plb_build", "plb_build_batch", "plb_query_batch", "plb_query_multi",
-            "plb_labels_view", "plb_labels_stats", "plb_labels_bytes", "plb_labels_free", "plb_degree_order",
+            "plb_labels_view", "plb_labels_stats", "plb_labels_bytes", "plb_labels_free", "plb_release_cached_memory",
+            "plb_degree_order",
             "plb_degree_order_noalloc", "plb_strerror", "plb_version"]
 
 
@@ -368,6 +371,11 @@ def degree_order_noalloc(row_ptr: torch.Tensor, out: torch.Tensor | None = None,
     _check(_lib().plb_degree_order_noalloc(ctypes.byref(g), out.data_ptr() if n else None, _stream(stream)),
            "plb_degree_order_noalloc")
     return out
+
+
+def release_cached_memory():
+    """Return the library's cached, unused device memory to the driver."""
+    _check(_lib().plb_release_cached_memory(), "plb_release_cached_memory")
 
 
 def version() -> int:
