@@ -238,7 +238,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     const int w_log_m = ceil_log2_i64(2 * warp_label);
     const int warps_per_block = kGpWarpThreads / 32;
     const size_t w_smem = sizeof(uint32_t) * (4 * warps_per_block +
-                                              (size_t)warps_per_block * ((1 << w_log_s) + (1 << w_log_m) + warp_cand));
+                                              (size_t)warps_per_block * ((1 << w_log_s) + (1 << w_log_m)));
     const int bthr = std::min(512, std::max(64, (o.block_threads / 32) * 32));
     const int block_cand = pow2_at_least(std::max(bthr, o.block_cand_cap));
     const int b_log_s = ceil_log2_i64(2 * (int64_t)block_cand);
@@ -256,6 +256,14 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_gp_block, bthr, b_smem);
     const int grid_w = sms * std::max(1, occ_w);
     const int grid_b = sms * std::max(1, occ_b);
+    // long frontier rows: block-per-row sort (power-of-two scratch per block)
+    int32_t* big = pool.alloc<int32_t>(n);
+    const int sort_blocks = 8;
+    const int64_t sort_words = pow2_at_least(std::max<int64_t>(n, 1));
+    uint32_t* sortscr = pool.alloc<uint32_t>(sort_words * sort_blocks);
+    PLB_ALLOC_OK();
+    PLB_CK(cudaFuncSetAttribute(k_sort_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(16384 * sizeof(uint32_t))));
     // block tier: per-block buffer of accepted hubs (at most v < n per vertex)
     uint32_t* gacc = pool.alloc<uint32_t>((int64_t)grid_b * std::max<int64_t>(n, 1));
     PLB_ALLOC_OK();
@@ -384,13 +392,17 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             PLB_ALLOC_OK();
         }
         k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[cur], fse[nxt], n, tmp64, A, ctr);
+        // sort the new frontier rows (appended unsorted by the gather/prune kernels)
+        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[nxt], fhub[nxt], A, ctr, big);
+        k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[nxt], fhub[nxt], big, ctr,
+                                                                            sortscr, sort_words);
         PLB_CK(exclusive_scan_i64(tmp64, loff[nxt], n, scan_scr, s));
         k_merge_old<<<grid_for((T + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(
             loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], n);
         k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
             loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], A, ctr, (uint32_t)d, top);
         PLB_CK(cudaGetLastError());
-        st.launches += 5;
+        st.launches += 7;
         T = Tn;
         cur = nxt;
         {

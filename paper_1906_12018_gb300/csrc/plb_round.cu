@@ -237,6 +237,31 @@ __device__ __forceinline__ uint32_t row_find(const uint32_t* r, int64_t len, uin
     return kEmpty;
 }
 
+constexpr int kPrefilterMinItems = 12;  // prefilter only candidates with longer checks
+
+// Top-hub witness prefilter for the 32 candidates of a chunk (one per lane):
+// candidate h has a witness among the kTopHubs highest-ranked hubs iff some
+// byte position w has top[v][w] + top[h][w] <= d (saturating byte add; 255 =
+// not a hub).  Each lane holds 8 bytes of v's row (tv0, tv1); the warp tests
+// one candidate per step with one coalesced 256-byte load.  Returns the mask
+// of lanes whose candidate is pruned.
+__device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, uint32_t tv0, uint32_t tv1, uint32_t d,
+                                                  uint32_t h, bool valid) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t dd = d * 0x01010101u;
+    // d <= 254 keeps "absent" (255, saturated) above every threshold
+    unsigned todo = __ballot_sync(kFull, valid && d <= 254u), pruned = 0;
+    while (todo) {
+        const int k = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const uint32_t hk = __shfl_sync(kFull, h, k);
+        const uint2 th = *reinterpret_cast<const uint2*>(top + (int64_t)hk * kTopHubs + 8 * lane);
+        const uint32_t hit = __vcmpleu4(__vaddus4(th.x, tv0), dd) | __vcmpleu4(__vaddus4(th.y, tv1), dd);
+        if (__any_sync(kFull, hit != 0)) pruned |= 1u << k;
+    }
+    return pruned;
+}
+
 // Distance check of up to 32 candidates held one per lane (valid lanes).
 // A witness for candidate h is a hub w of both v and h with
 // d(w,v) + d(w,h) <= d (the test of Alg. 3 with the labels of round d-1).
@@ -251,7 +276,8 @@ __device__ __forceinline__ uint32_t row_find(const uint32_t* r, int64_t len, uin
 // whose candidate survives.
 __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_t* M, int log_m, const uint32_t* lv,
                                                 int64_t lvlen, uint32_t h, bool valid, unsigned* pm_sm,
-                                                unsigned long long& probed) {
+                                                unsigned long long& probed, uint32_t tv0, uint32_t tv1,
+                                                unsigned long long& prefiltered) {
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
@@ -269,6 +295,13 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
                 meta = __ffs((int)(x1 - x0));  // log2 + 1
             }
         }
+    }
+    // candidates with a long check first try the top-hub prefilter
+    const unsigned pf = top_prefilter(p.top, tv0, tv1, p.d, h, valid && items >= kPrefilterMinItems);
+    if (lane == 0) prefiltered += __popc(pf);
+    if ((pf >> lane) & 1u) {
+        valid = false;
+        items = 0;
     }
     const unsigned vmask = __ballot_sync(kFull, valid);
     if (lane == 0) *pm_sm = 0;
@@ -304,29 +337,6 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
     const unsigned pm = *(volatile unsigned*)pm_sm;
     __syncwarp();
     return vmask & ~pm;
-}
-
-// Top-hub witness prefilter for the 32 candidates of a chunk (one per lane):
-// candidate h has a witness among the kTopHubs highest-ranked hubs iff some
-// byte position w has top[v][w] + top[h][w] <= d (saturating byte add; 255 =
-// not a hub).  Each lane holds 8 bytes of v's row (tv0, tv1); the warp tests
-// one candidate per step with one coalesced 256-byte load.  Returns the mask
-// of lanes whose candidate is pruned.
-__device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, uint32_t tv0, uint32_t tv1, uint32_t d,
-                                                  uint32_t h, bool valid) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t dd = d * 0x01010101u;
-    // d <= 254 keeps "absent" (255, saturated) above every threshold
-    unsigned todo = __ballot_sync(kFull, valid && d <= 254u), pruned = 0;
-    while (todo) {
-        const int k = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint32_t hk = __shfl_sync(kFull, h, k);
-        const uint2 th = *reinterpret_cast<const uint2*>(top + (int64_t)hk * kTopHubs + 8 * lane);
-        const uint32_t hit = __vcmpleu4(__vaddus4(th.x, tv0), dd) | __vcmpleu4(__vaddus4(th.y, tv1), dd);
-        if (__any_sync(kFull, hit != 0)) pruned |= 1u << k;
-    }
-    return pruned;
 }
 
 // Gather of v's messages with hub in [lo, hi) (hi <= v: only hubs that
@@ -382,18 +392,17 @@ __device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int6
 // One warp per vertex (tables in shared memory):
 //  1. stage L(v) into the hub-keyed map M;
 //  2. gather the unique messages into the set S;
-//  3. check them 32 at a time (check_chunk);
-//  4. sort the accepted hubs and append them to the new frontier.
+//  3. compact S in place and check the candidates 32 at a time;
+//  4. append the accepted hubs (unsorted) to the new frontier.
 // A vertex whose unique candidates exceed cand_limit goes to the block tier.
 __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
     extern __shared__ uint32_t sm[];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int S_CAP = 1 << p.log_s, M_CAP = 1 << p.log_m, ACC = p.cand_limit;
+    const int S_CAP = 1 << p.log_s, M_CAP = 1 << p.log_m;
     int* wsc = reinterpret_cast<int*>(sm) + wib * 4;  // [0] unique count [1] overflow [3] pruned mask
-    uint32_t* S = sm + 4 * nwarps + wib * (S_CAP + M_CAP + ACC);
+    uint32_t* S = sm + 4 * nwarps + wib * (S_CAP + M_CAP);
     uint32_t* M = S + S_CAP;
-    uint32_t* C = M + M_CAP;
     unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
     unsigned long long c_pref = 0;
     const int nlist = *p.list_n;
@@ -428,13 +437,14 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
             c_vert += 1;
             c_uniq += nS;
         }
-        // compact the set into C
+        // compact the set in place (write position never passes the read position)
         int nc = 0;
         for (int sb = 0; sb < S_CAP; sb += 32) {
             const uint32_t h = S[sb + lane];
+            __syncwarp();
             const bool has = h != kEmpty;
             const unsigned m = __ballot_sync(kFull, has);
-            if (has) C[nc + __popc(m & ((1u << lane) - 1u))] = h;
+            if (has) S[nc + __popc(m & ((1u << lane) - 1u))] = h;
             nc += __popc(m);
         }
         __syncwarp();
@@ -442,28 +452,21 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
         const uint2 tv = *reinterpret_cast<const uint2*>(p.top + (int64_t)v * kTopHubs + 8 * lane);
         int nacc = 0;
         for (int cb = 0; cb < nc; cb += 32) {
-            bool valid = cb + lane < nc;
-            const uint32_t h = valid ? C[cb + lane] : 0u;
+            const bool valid = cb + lane < nc;
+            const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned pf = top_prefilter(p.top, tv.x, tv.y, p.d, h, valid);
-            if (lane == 0) c_pref += __popc(pf);
-            valid = valid && !((pf >> lane) & 1u);
-            const unsigned okm = check_chunk(p, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3], c_probed);
-            if ((okm >> lane) & 1u) C[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
+            const unsigned okm = check_chunk(p, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3], c_probed,
+                                             tv.x, tv.y, c_pref);
+            if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
         }
         if (nacc > 0) {
-            int P = 1;
-            while (P < nacc) P <<= 1;
-            for (int s = nacc + lane; s < P; s += 32) C[s] = kEmpty;
-            __syncwarp();
-            group_bitonic_sort(C, P, lane, 32, WarpSync());
             unsigned long long start = 0;
             if (lane == 0) start = atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
             start = __shfl_sync(kFull, start, 0);
             if (start + nacc <= p.fcap) {
-                for (int j = lane; j < nacc; j += 32) p.fhub_new[start + j] = C[j];
+                for (int j = lane; j < nacc; j += 32) p.fhub_new[start + j] = S[j];
                 if (lane == 0) p.fse_new[v] = fpack(start, (uint32_t)nacc);
             } else if (lane == 0) {
                 p.ctr->fovf = 1;
@@ -492,9 +495,8 @@ enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_START = 6 /* 2 ints */
 // One block per vertex, any size.  The candidates are processed in passes
 // over hub ranges [lo, hi): each pass gathers the messages of its range into
 // the shared-memory set (a pass whose set overflows is retried on half the
-// range), checks them and appends the sorted survivors to this block's
-// global scratch; passes run in increasing hub order, so the concatenation
-// is sorted.  L(v) is staged into the shared-memory map when it fits;
+// range), checks them and appends the survivors to this block's global
+// scratch, copied to the new frontier at the end.  L(v) is staged into the shared-memory map when it fits;
 // otherwise membership in L(v) is a binary search in its row.
 __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
                                 uint32_t* gacc, int* sh, unsigned long long* cnt) {
@@ -556,32 +558,20 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
         const int nc = *(volatile int*)&sh[SH_NC];
         if (tid == 0) cnt[2] += nc;
         // distance checks: warp w takes candidate chunks w, w + nw, ...; the
-        // survivors are appended to Acc (the set's storage, free by now)
-        uint32_t* Acc = S;
+        // survivors are appended (unsorted) to this block's scratch
         for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
             bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
             if (!useM && valid && row_find(lv, ll, h) != kEmpty) valid = false;  // already a hub of v
-            const unsigned pf = top_prefilter(p.top, tv.x, tv.y, p.d, h, valid);
-            if (lane == 0) cnt[7] += __popc(pf);
-            valid = valid && !((pf >> lane) & 1u);
-            const unsigned okm = check_chunk(p, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4]);
+            const unsigned okm = check_chunk(p, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4],
+                                             tv.x, tv.y, cnt[7]);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
             base = __shfl_sync(kFull, base, 0);
-            if ((okm >> lane) & 1u) Acc[base + __popc(okm & ((1u << lane) - 1u))] = h;
+            if ((okm >> lane) & 1u) gacc[total_acc + base + __popc(okm & ((1u << lane) - 1u))] = h;
         }
         __syncthreads();
-        const int nacc = *(volatile int*)&sh[SH_ACC];
-        if (nacc > 0) {
-            int P = 1;
-            while (P < nacc) P <<= 1;
-            for (int s = nacc + tid; s < P; s += nthr) Acc[s] = kEmpty;
-            __syncthreads();
-            group_bitonic_sort(Acc, P, tid, nthr, BlockSync());
-            for (int j = tid; j < nacc; j += nthr) gacc[total_acc + j] = Acc[j];
-            total_acc += nacc;
-        }
+        total_acc += *(volatile int*)&sh[SH_ACC];
         __syncthreads();
         width = 2 * (int64_t)(hi - lo);
         lo = hi;
@@ -688,6 +678,78 @@ __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int6
             base = __shfl_sync(am, base, leader);
             if (act) A[base + __popc(m & ((1u << lane_id()) - 1u))] = (int32_t)v;
         }
+    }
+}
+
+// ------------------------------------------------- sort new frontier rows
+// The gather/prune kernels append each vertex's accepted hubs unsorted; one
+// warp per active vertex sorts its row: up to 32 entries in registers (a
+// bitonic network over the lanes), up to kWarpSortMax in shared memory;
+// longer rows are listed for k_sort_rows_block.
+constexpr int kWarpSortMax = 1024;
+constexpr int kSortWarps = 8;
+
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new,
+                                                                   const int32_t* A, RoundCounters* ctr,
+                                                                   int32_t* big) {
+    __shared__ uint32_t buf[kSortWarps][kWarpSortMax];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int nA = ctr->nA;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += nw) {
+        const int32_t v = A[i];
+        const uint64_t f = fse_new[v];
+        const int c = (int)fcount(f);
+        uint32_t* row = fhub_new + fstart(f);
+        if (c <= 1) continue;
+        if (c <= 32) {
+            uint32_t x = lane < c ? row[lane] : kEmpty;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const uint32_t y = __shfl_xor_sync(kFull, x, j);
+                    const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                    x = (lower == up) ? min(x, y) : max(x, y);
+                }
+            }
+            if (lane < c) row[lane] = x;
+        } else if (c <= kWarpSortMax) {
+            int P = 64;
+            while (P < c) P <<= 1;
+            uint32_t* b = buf[w];
+            for (int j = lane; j < P; j += 32) b[j] = j < c ? row[j] : kEmpty;
+            __syncwarp();
+            group_bitonic_sort(b, P, lane, 32, WarpSync());
+            for (int j = lane; j < c; j += 32) row[j] = b[j];
+            __syncwarp();
+        } else if (lane == 0) {
+            big[atomicAdd(&ctr->nBig, 1)] = v;
+        }
+    }
+}
+
+// One block per long row: bitonic sort in a power-of-two buffer (shared
+// memory up to kBlockSortSmem entries, else this block's global scratch).
+constexpr int kBlockSortSmem = 16384;
+
+__global__ void __launch_bounds__(1024) k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new,
+                                                          const int32_t* big, const RoundCounters* ctr,
+                                                          uint32_t* scratch, int64_t scratch_words) {
+    extern __shared__ uint32_t sbuf[];
+    const int nBig = ctr->nBig;
+    for (int i = blockIdx.x; i < nBig; i += gridDim.x) {
+        const uint64_t f = fse_new[big[i]];
+        const int64_t c = fcount(f);
+        uint32_t* row = fhub_new + fstart(f);
+        int64_t P = 1;
+        while (P < c) P <<= 1;
+        uint32_t* b = P <= kBlockSortSmem ? sbuf : scratch + (int64_t)blockIdx.x * scratch_words;
+        for (int64_t j = threadIdx.x; j < P; j += blockDim.x) b[j] = j < c ? row[j] : kEmpty;
+        __syncthreads();
+        group_bitonic_sort(b, (int)P, threadIdx.x, blockDim.x, BlockSync());
+        for (int64_t j = threadIdx.x; j < c; j += blockDim.x) row[j] = b[j];
+        __syncthreads();
     }
 }
 
