@@ -258,6 +258,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     const int grid_b = sms * std::max(1, occ_b);
     // long frontier rows: block-per-row sort (power-of-two scratch per block)
     int32_t* big = pool.alloc<int32_t>(n);
+    int32_t* giant = pool.alloc<int32_t>(n);
     const int sort_blocks = 8;
     const int64_t sort_words = pow2_at_least(std::max<int64_t>(n, 1));
     uint32_t* sortscr = pool.alloc<uint32_t>(sort_words * sort_blocks);
@@ -393,16 +394,18 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
         k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[cur], fse[nxt], n, tmp64, A, ctr);
         // sort the new frontier rows (appended unsorted by the gather/prune kernels)
-        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[nxt], fhub[nxt], A, ctr, big);
-        k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[nxt], fhub[nxt], big, ctr,
-                                                                            sortscr, sort_words);
+        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[nxt], fhub[nxt], A, ctr, big, giant);
+        k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(fse[nxt], fhub[nxt], big, &ctr->nBig,
+                                                                        nullptr, 0);
+        k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[nxt], fhub[nxt], giant,
+                                                                            &ctr->nGiant, sortscr, sort_words);
         PLB_CK(exclusive_scan_i64(tmp64, loff[nxt], n, scan_scr, s));
         k_merge_old<<<grid_for((T + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(
             loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], n);
         k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
             loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], A, ctr, (uint32_t)d, top);
         PLB_CK(cudaGetLastError());
-        st.launches += 7;
+        st.launches += 9;
         T = Tn;
         cur = nxt;
         {

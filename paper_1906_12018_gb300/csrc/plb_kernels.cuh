@@ -26,7 +26,7 @@ struct RoundCounters {
     unsigned long long bound_sum; // sum over receivers of the candidate bound min(v, messages)
     unsigned long long prefiltered; // candidates pruned by the top-hub witness prefilter
     int nR, nO1, nO2;             // receivers: warp tier, block tier (nO2 unused)
-    int nBig;                     // new frontier rows too long for a warp to sort
+    int nBig, nGiant;             // new frontier rows too long for a warp / for shared memory to sort
     int nA;                       // next active list (kept across the per-round reset)
     int nO1_base, nO2_base;       // tier-list sizes made by k_collect (for reruns)
     int fovf;                     // new-frontier buffer overflow

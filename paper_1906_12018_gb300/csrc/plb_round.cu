@@ -688,10 +688,11 @@ __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int6
 // longer rows are listed for k_sort_rows_block.
 constexpr int kWarpSortMax = 1024;
 constexpr int kSortWarps = 8;
+constexpr int kBlockSortSmem = 16384;
 
 __global__ void __launch_bounds__(kSortWarps * 32) k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new,
                                                                    const int32_t* A, RoundCounters* ctr,
-                                                                   int32_t* big) {
+                                                                   int32_t* big, int32_t* giant) {
     __shared__ uint32_t buf[kSortWarps][kWarpSortMax];
     const int lane = lane_id(), w = threadIdx.x >> 5;
     const int nA = ctr->nA;
@@ -724,20 +725,21 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_rows_warp(const uint64
             for (int j = lane; j < c; j += 32) row[j] = b[j];
             __syncwarp();
         } else if (lane == 0) {
-            big[atomicAdd(&ctr->nBig, 1)] = v;
+            if (c <= kBlockSortSmem) big[atomicAdd(&ctr->nBig, 1)] = v;
+            else giant[atomicAdd(&ctr->nGiant, 1)] = v;
         }
     }
 }
 
 // One block per long row: bitonic sort in a power-of-two buffer (shared
-// memory up to kBlockSortSmem entries, else this block's global scratch).
-constexpr int kBlockSortSmem = 16384;
+// memory for rows up to kBlockSortSmem entries; longer rows use this block's
+// global scratch).  Launched once for each list.
 
 __global__ void __launch_bounds__(1024) k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new,
-                                                          const int32_t* big, const RoundCounters* ctr,
+                                                          const int32_t* big, const int* nbig,
                                                           uint32_t* scratch, int64_t scratch_words) {
     extern __shared__ uint32_t sbuf[];
-    const int nBig = ctr->nBig;
+    const int nBig = *nbig;
     for (int i = blockIdx.x; i < nBig; i += gridDim.x) {
         const uint64_t f = fse_new[big[i]];
         const int64_t c = fcount(f);

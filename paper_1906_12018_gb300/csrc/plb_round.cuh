@@ -32,9 +32,9 @@ __global__ void k_index_fill(const int64_t* loff, const uint32_t* lent, const in
 __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int64_t n, int64_t* newlen, int32_t* A,
                               RoundCounters* ctr);
 __global__ void k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* A, RoundCounters* ctr,
-                                 int32_t* big);
-__global__ void k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* big,
-                                  const RoundCounters* ctr, uint32_t* scratch, int64_t scratch_words);
+                                 int32_t* big, int32_t* giant);
+__global__ void k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* big, const int* nbig,
+                                  uint32_t* scratch, int64_t scratch_words);
 __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
                             const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n);
 __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
