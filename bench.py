@@ -341,14 +341,16 @@ def main():
             "config": {"workload": args.workload, "n": g.n, "m": g.m, "labels": n_labels,
                        "rounds": st0["rounds"], "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "gather+prune (k_gp_warp/k_gp_block/k_gp_global)",
+            "roofline": {"bound": "hbm", "kernel": "gather+prune (k_gp_warp + k_gp_block)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
                          "traffic": None, "algorithmic_bytes": gp_bytes, "kernel_ms": gp_ms,
                          "build_ms_profiled": st["ms_total"]},
             "kernel_ms": {"prepare": st["ms_prepare"], "frontier": st["ms_frontier"],
-                          "gather_prune": st["ms_gather_prune"], "merge": st["ms_merge"],
+                          "gather_prune": st["ms_gather_prune"][:2], "merge_sort_index": st["ms_merge"],
                           "finalize": st["ms_finalize"]},
+            "counters": {k: st[k] for k in ("receivers", "messages_round", "unique_round", "prefiltered_round",
+                                            "probed_round", "accepted", "tier_vertices", "launches")},
             "e2e": {"value": g.m * world / (e2e_ms_med / 1e3), "unit": "edges/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_med},
             "queries": {"value": q_value, "unit": "queries/s", "batch": 1 << 16,
