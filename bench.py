@@ -204,6 +204,128 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """2,000 small graphs (sizes log-uniform 1k-64k; half R-MAT edge factor 8,
+    half Chung-Lu gamma 2.3 mean degree 10; seeds 100-2099): one plb_build
+    per graph vs plb_build_batch over all of them (tuned and default tier
+    geometry)."""
+    import torch
+
+    from paper_1906_12018_gb300 import autotune
+    from paper_1906_12018_gb300 import graphs as G
+    from paper_1906_12018_gb300 import plb
+
+    dev = torch.device("cuda", 0)
+    k = args.batch_graphs
+    gs = [G.small_graph(i) for i in range(k)]
+    devs = [(torch.from_numpy(g.off).to(dev), torch.from_numpy(g.col).to(dev),
+             torch.from_numpy(G.degree_order(g)).to(dev)) for g in gs]
+    m = sum(g.m for g in gs)
+    opts = plb.default_options()
+    tuned, tune_report = autotune.tune_batch(devs[: min(k, 200)])
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        fn()
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t
+
+    def loop():
+        for d in devs:
+            plb.build(*d, opts).free()
+
+    def batch(o):
+        def f():
+            for lab in plb.build_batch(devs, o):
+                lab.free()
+        return f
+
+    for _ in range(max(args.warmup, 1)):
+        timed(batch(opts))
+    t_loop = min(timed(loop) for _ in range(2))
+    t_def = min(timed(batch(opts)) for _ in range(max(args.steps, 1)))
+    t_tuned = min(timed(batch(tuned)) for _ in range(max(args.steps, 1)))
+    line = {"metric": "labeling edges/sec", "value": m / t_tuned, "unit": "edges/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tuned, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batch{k}", "graphs": k, "n": sum(g.n for g in gs), "m": m},
+            "one_graph_at_a_time": {"value": m / t_loop, "ms": 1e3 * t_loop},
+            "batched_default": {"value": m / t_def, "ms": 1e3 * t_def},
+            "batched_tuned": {"value": m / t_tuned, "ms": 1e3 * t_tuned, "options": autotune.as_dict(tuned)},
+            "speedup_vs_one_at_a_time": t_loop / t_tuned, "autotune": tune_report}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Serving: R-MAT scale-22 labels resident; labeling jobs drawn from the
+    small-graph distribution; query requests with Poisson arrivals and
+    uniform 1..65,536 pairs (seed 4), at several offered loads."""
+    import threading
+
+    import torch
+
+    from paper_1906_12018_gb300 import graphs as G
+    from paper_1906_12018_gb300 import plb
+    from paper_1906_12018_gb300.serve import LabelServer, latency_summary
+
+    dev = torch.device("cuda", 0)
+    g = G.workload(args.serve_resident)
+    order = G.degree_order(g)
+    base = plb.build(torch.from_numpy(g.off).to(dev), torch.from_numpy(g.col).to(dev),
+                     torch.from_numpy(order).to(dev))
+    jobs = [G.small_graph(i) for i in range(args.serve_jobs)]
+    results = []
+    for rate in args.serve_rates:
+        srv = LabelServer(build_slots=2, max_inflight=2)
+        srv.add_resident("base", base)
+        stop = time.perf_counter() + args.serve_seconds
+        rng = np.random.default_rng(4)
+        reqs = []
+
+        def jobs_client():
+            i = 0
+            while time.perf_counter() < stop and i < len(jobs):
+                gi = jobs[i]
+                srv.submit_build(f"job{i}", gi.off, gi.col, G.degree_order(gi))
+                i += 1
+                time.sleep(args.serve_job_interval)
+
+        jt = threading.Thread(target=jobs_client)
+        jt.start()
+        t_next = time.perf_counter()
+        while time.perf_counter() < stop:
+            t_next += rng.exponential(1.0 / rate)
+            delay = t_next - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            q = int(rng.integers(1, 65537))
+            reqs.append(srv.submit_query("base", rng.integers(0, g.n, (q, 2)).astype(np.int32)))
+        jt.join()
+        srv.wait_idle()
+        st = latency_summary(reqs)
+        st["offered_requests_per_s"] = rate
+        st["jobs_done"] = len(srv.completed_builds)
+        results.append(st)
+        for nm in list(srv.sets):
+            if nm != "base":
+                srv.drop(nm)
+        srv.sets.pop("base")
+        srv.close()
+    best = max(results, key=lambda r: r["queries_per_s"])
+    line = {"metric": "queries/sec with p50/p99 latency", "value": best["queries_per_s"], "unit": "queries/s",
+            "n_gpus": 1, "steps": len(results), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"serve-{args.serve_resident}", "n": g.n, "m": g.m, "labels": base.total,
+                       "request_pairs": "uniform 1..65536", "arrivals": "poisson", "seconds": args.serve_seconds,
+                       "job_interval_s": args.serve_job_interval},
+            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "loads": results}
+    print(json.dumps(line), flush=True)
+    base.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,9 +337,20 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--mode", default="build", choices=["build", "batch", "serve"])
+    ap.add_argument("--batch-graphs", type=int, default=2000)
+    ap.add_argument("--serve-resident", default="rmat22")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 3200.0])
+    ap.add_argument("--serve-jobs", type=int, default=400)
+    ap.add_argument("--serve-job-interval", type=float, default=0.02)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     import torch
 
