@@ -210,6 +210,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int64_t hcap = std::max<int64_t>(4 * n, 1024);
     uint32_t* htab = pool.alloc<uint32_t>(hcap);
     PLB_ALLOC_OK();
+    PLB_CK(cudaFuncSetAttribute(k_index_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(8 * 2048 * sizeof(uint32_t))));
     auto build_index = [&](int which, int64_t total) -> int {
         if (4 * total > hcap) {
             pool.release(htab);
@@ -219,10 +221,9 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
         k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[which], n, tmp64);
         if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
-        k_index_clear<<<flat_grid_cap, kFlatThreads, 0, s>>>(htab, hoff + n);
-        k_index_fill<<<grid_for((total + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(loff[which],
-                                                                                             lent[which], hoff, htab, n);
-        st.launches += 5;
+        k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t), s>>>(
+            loff[which], lent[which], hoff, htab, n);
+        st.launches += 4;
         return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
     };
     {
@@ -243,7 +244,9 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     const int block_cand = pow2_at_least(std::max(bthr, o.block_cand_cap));
     const int b_log_s = ceil_log2_i64(2 * (int64_t)block_cand);
     const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);
-    const size_t b_smem = sizeof(uint32_t) * (48 + (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) + block_cand);
+    // scalars (48) + warp sums (34) + prefix per thread + 64-bit row start per thread + tables
+    const size_t b_smem = sizeof(uint32_t) * (48 + 34 + (size_t)((bthr + 2) & ~1) + 2 * (size_t)bthr +
+                                              (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) + block_cand);
     TierLimits lim;
     lim.warp_bound = 2 * (int64_t)warp_cand;
     lim.warp_label = warp_label;

@@ -389,6 +389,85 @@ __device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int6
     return true;
 }
 
+// Block-wide exclusive scan of one int per thread (blockDim <= 1024);
+// wsum is shared scratch of 32 ints.  Returns the thread's exclusive prefix
+// and the block total in *total.
+__device__ __forceinline__ int block_excl_scan(int x, int* wsum, int* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int incl = warp_incl_scan(x, lane);
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int w = lane < nw ? wsum[lane] : 0;
+        const int wi = warp_incl_scan(w, lane);
+        wsum[lane] = wi - w;
+        if (lane == 31) wsum[32] = wi;
+    }
+    __syncthreads();
+    const int r = wsum[wid] + incl - x;
+    *total = wsum[32];
+    return r;
+}
+
+// Block-wide load-balanced gather of v's messages with hub in [lo, hi) into
+// S: neighbours are taken in tiles of blockDim; each thread finds its
+// neighbour's sub-range of dL_{d-1}(a) (binary searches in the sorted row), a
+// block-wide exclusive scan of the counts assigns every thread an equal,
+// contiguous share of the tile's messages.  Returns false on overflow.
+__device__ bool gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t lo, uint32_t hi, uint32_t* S,
+                             int log_s, const uint32_t* M, int log_m, int limit, int* cnt_sm, volatile int* ovf_sm,
+                             int* wsum, int* sex, int64_t* sst, unsigned long long& msgs) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int64_t t0 = nb; t0 < ne; t0 += nthr) {
+        const int64_t j = t0 + tid;
+        int c = 0;
+        int64_t st = 0;
+        if (j < ne) {
+            const uint64_t f = p.fse[p.rcol[j]];
+            const uint32_t n0 = fcount(f);
+            if (n0) {
+                const uint32_t* row = p.fhub + fstart(f);
+                const int64_t a0 = lo ? lower_bound_u32(row, n0, lo) : 0;
+                const int64_t a1 = lower_bound_u32(row, n0, hi);
+                st = (int64_t)fstart(f) + a0;
+                c = (int)(a1 - a0);
+            }
+        }
+        int total;
+        const int excl = block_excl_scan(c, wsum, &total);
+        sex[tid] = excl;
+        sst[tid] = st;
+        if (tid == 0) sex[nthr] = total;
+        __syncthreads();
+        const int per = (total + nthr - 1) / nthr;
+        const int beg = tid * per, end = min(total, beg + per);
+        if (beg < end) {
+            int k = 0, hk = nthr - 1;  // largest k with sex[k] <= beg
+            while (k < hk) {
+                const int mid = (k + hk + 1) >> 1;
+                if (sex[mid] <= beg) k = mid; else hk = mid - 1;
+            }
+            for (int it = beg; it < end; ++it) {
+                while (it >= sex[k + 1]) ++k;
+                const uint32_t h = p.fhub[sst[k] + (it - sex[k])];
+                if (!M || map_find(M, log_m, h) == kEmpty) {
+                    if (*(volatile int*)cnt_sm >= limit) {
+                        *ovf_sm = 1;
+                        break;
+                    } else if (set_insert(S, log_s, h)) {
+                        atomicAdd(cnt_sm, 1);
+                    }
+                }
+                if (*ovf_sm) break;
+            }
+        }
+        if (tid == 0) msgs += total;
+        __syncthreads();
+        if (*ovf_sm) return false;
+    }
+    return true;
+}
+
 // One warp per vertex (tables in shared memory):
 //  1. stage L(v) into the hub-keyed map M;
 //  2. gather the unique messages into the set S;
@@ -499,7 +578,8 @@ enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_START = 6 /* 2 ints */
 // scratch, copied to the new frontier at the end.  L(v) is staged into the shared-memory map when it fits;
 // otherwise membership in L(v) is a binary search in its row.
 __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
-                                uint32_t* gacc, int* sh, unsigned long long* cnt) {
+                                uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst,
+                                unsigned long long* cnt) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
     const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
@@ -534,8 +614,8 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
             sh[SH_NC] = 0;
         }
         __syncthreads();
-        gather_range(p, nb + 32 * wid, ne, 32 * nw, lo, hi, S, log_s, Mp, log_m, limit, &sh[SH_UNIQ],
-                     (volatile int*)&sh[SH_OVF], cnt[1]);
+        gather_block(p, nb, ne, lo, hi, S, log_s, Mp, log_m, limit, &sh[SH_UNIQ], (volatile int*)&sh[SH_OVF],
+                     wsum, sex, sst, cnt[1]);
         __syncthreads();
         const int nS = *(volatile int*)&sh[SH_UNIQ];
         if (*(volatile int*)&sh[SH_OVF] || nS > limit) {
@@ -597,14 +677,17 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
 __global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
     extern __shared__ uint32_t sm[];
     int* sh = reinterpret_cast<int*>(sm);
-    uint32_t* S = sm + SH_WORDS;
+    int* wsum = sh + SH_WORDS;                                      // 33 ints (+ pad)
+    int* sex = wsum + 34;                                           // blockDim + 1 ints
+    int64_t* sst = reinterpret_cast<int64_t*>(sex + ((blockDim.x + 2) & ~1u));  // blockDim int64
+    uint32_t* S = reinterpret_cast<uint32_t*>(sst + blockDim.x);
     uint32_t* M = S + (1 << p.log_s);
     uint32_t* C = M + (1 << p.log_m);
     uint32_t* gacc = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
     unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int n1 = *p.list_n;
     for (int i = blockIdx.x; i < n1; i += gridDim.x) {
-        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, cnt);
+        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, cnt);
         __syncthreads();
     }
     cnt[1] = warp_sum(cnt[1]);
@@ -657,6 +740,47 @@ __global__ void k_index_fill(const int64_t* loff, const uint32_t* lent, const in
             const int64_t x = row_of(loff, r0, r1, q);
             const int64_t b = hoff[x], sz = hoff[x + 1] - b;
             if (sz > 0) map_insert(htab + b, __ffs((int)sz) - 1, lent[q]);
+        }
+    }
+}
+
+// One warp per indexed row: the table is built in shared memory (rows whose
+// table has up to kIndexSmemSlots slots) and written out whole, empty slots
+// included; larger tables are cleared and filled in place with atomics.
+constexpr int kIndexWarps = 8;
+constexpr int kIndexSmemSlots = 2048;
+
+__global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t* loff, const uint32_t* lent,
+                                                                  const int64_t* hoff, uint32_t* htab, int64_t n) {
+    extern __shared__ uint32_t ibuf[];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    uint32_t* buf = ibuf + w * kIndexSmemSlots;
+    const int64_t nwarps = (int64_t)gridDim.x * kIndexWarps;
+    for (int64_t base = ((int64_t)blockIdx.x * kIndexWarps + w) * 32; base < n; base += nwarps * 32) {
+        const int64_t x = base + lane;
+        int64_t hb = 0, P = 0;
+        if (x < n) {
+            hb = hoff[x];
+            P = hoff[x + 1] - hb;
+        }
+        unsigned m = __ballot_sync(kFull, P > 0);
+        while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1;
+            const int64_t xk = base + k;
+            const int64_t hbk = __shfl_sync(kFull, hb, k);
+            const int Pk = (int)__shfl_sync(kFull, P, k);
+            const int lg = __ffs(Pk) - 1;
+            const int64_t lb = loff[xk], ll = loff[xk + 1] - lb;
+            uint32_t* tab = Pk <= kIndexSmemSlots ? buf : htab + hbk;
+            for (int sl = lane; sl < Pk; sl += 32) tab[sl] = kEmpty;
+            __syncwarp();
+            for (int64_t j = lane; j < ll; j += 32) map_insert(tab, lg, lent[lb + j]);
+            __syncwarp();
+            if (Pk <= kIndexSmemSlots) {
+                for (int sl = lane; sl < Pk; sl += 32) htab[hbk + sl] = buf[sl];
+                __syncwarp();
+            }
         }
     }
 }

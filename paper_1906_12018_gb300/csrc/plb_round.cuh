@@ -29,6 +29,8 @@ __global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz);
 __global__ void k_index_clear(uint32_t* htab, const int64_t* hoff_n);
 __global__ void k_index_fill(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
                              int64_t n);
+__global__ void k_index_build(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
+                              int64_t n);
 __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int64_t n, int64_t* newlen, int32_t* A,
                               RoundCounters* ctr);
 __global__ void k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* A, RoundCounters* ctr,
