@@ -409,16 +409,72 @@ __device__ __forceinline__ int block_excl_scan(int x, int* wsum, int* total) {
     return r;
 }
 
-// Block-wide load-balanced gather of v's messages with hub in [lo, hi) into
-// S: neighbours are taken in tiles of blockDim; each thread finds its
+// Shrink the hub range of a pass whose set overflowed: histogram the keys of
+// S below hi over 256 buckets of [lo, hi) and cut hi at the first bucket where
+// the running count would pass half the capacity.  The kept count is read off
+// the histogram; when it fits (always, unless the first bucket alone is too
+// full, then the range is narrowed to that bucket and the histogram redone,
+// keys at or above hi being ignored), S is rebuilt from the kept keys (C is
+// scratch).  All threads call; returns with *hi_sm and *cnt_sm set.
+__device__ void shrink_pass(uint32_t* S, int log_s, uint32_t* C, int limit, uint32_t lo, uint32_t* hi_sm,
+                            int* cnt_sm, int* hist, int* tmp) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int S_CAP = 1 << log_s;
+    while (true) {
+        const uint32_t hi = *(volatile uint32_t*)hi_sm;
+        const uint32_t bw = (hi - lo + 255u) / 256u;
+        for (int b = tid; b < 256; b += nthr) hist[b] = 0;
+        __syncthreads();
+        for (int sl = tid; sl < S_CAP; sl += nthr) {
+            const uint32_t key = S[sl];
+            if (key != kEmpty && key < hi) atomicAdd(&hist[(key - lo) / bw], 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int cum = 0, b = 0;
+            while (b < 255 && cum + hist[b] <= limit / 2) cum += hist[b++];
+            if (b == 0) {  // the first bucket alone passes half the capacity: keep it whole
+                b = 1;
+                cum = hist[0];
+            }
+            uint32_t nh = lo + (uint32_t)b * bw;
+            if (nh > hi) nh = hi;
+            *hi_sm = nh;
+            tmp[0] = cum;  // keys below nh
+            tmp[1] = 0;
+        }
+        __syncthreads();
+        const uint32_t nh = *(volatile uint32_t*)hi_sm;
+        const int kept = *(volatile int*)&tmp[0];
+        if (kept > limit) continue;  // narrow further (S untouched; keys >= nh are ignored)
+        for (int sl = tid; sl < S_CAP; sl += nthr) {
+            const uint32_t key = S[sl];
+            if (key != kEmpty && key < nh) C[atomicAdd(&tmp[1], 1)] = key;
+        }
+        __syncthreads();
+        for (int sl = tid; sl < S_CAP; sl += nthr) S[sl] = kEmpty;
+        __syncthreads();
+        for (int q = tid; q < kept; q += nthr) set_insert(S, log_s, C[q]);
+        if (tid == 0) *cnt_sm = kept;
+        __syncthreads();
+        return;
+    }
+}
+
+// Block-wide load-balanced gather of v's messages with hub in [lo, *hi_sm)
+// into S: neighbours are taken in tiles of blockDim; each thread finds its
 // neighbour's sub-range of dL_{d-1}(a) (binary searches in the sorted row), a
 // block-wide exclusive scan of the counts assigns every thread an equal,
-// contiguous share of the tile's messages.  Returns false on overflow.
-__device__ bool gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t lo, uint32_t hi, uint32_t* S,
+// contiguous share of the tile's messages.  When the set would exceed
+// `limit`, the range is shrunk (shrink_pass) and the current tile redone, so
+// messages gathered below the new bound are kept.
+__device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t lo, uint32_t* hi_sm, uint32_t* S,
                              int log_s, const uint32_t* M, int log_m, int limit, int* cnt_sm, volatile int* ovf_sm,
-                             int* wsum, int* sex, int64_t* sst, unsigned long long& msgs) {
+                             int* wsum, int* sex, int64_t* sst, uint32_t* C, int* hist, int* tmp,
+                             unsigned long long& msgs) {
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int64_t t0 = nb; t0 < ne; t0 += nthr) {
+    for (int64_t t0 = nb; t0 < ne;) {
+        const uint32_t hi = *(volatile uint32_t*)hi_sm;
         const int64_t j = t0 + tid;
         int c = 0;
         int64_t st = 0;
@@ -463,9 +519,14 @@ __device__ bool gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
         }
         if (tid == 0) msgs += total;
         __syncthreads();
-        if (*ovf_sm) return false;
+        if (*ovf_sm) {
+            shrink_pass(S, log_s, C, limit, lo, hi_sm, cnt_sm, hist, tmp);
+            if (tid == 0) *ovf_sm = 0;
+            __syncthreads();
+            continue;  // redo this tile with the smaller range
+        }
+        t0 += nthr;
     }
-    return true;
 }
 
 // One warp per vertex (tables in shared memory):
@@ -568,17 +629,17 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
 }
 
 // Block-per-vertex scalars in shared memory (ints)
-enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_START = 6 /* 2 ints */,
+enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_HI = 4, SH_TMP = 5, SH_START = 6 /* 2 ints */,
        SH_PM = 16 /* one word per warp */, SH_WORDS = 48 };
 
 // One block per vertex, any size.  The candidates are processed in passes
 // over hub ranges [lo, hi): each pass gathers the messages of its range into
-// the shared-memory set (a pass whose set overflows is retried on half the
-// range), checks them and appends the survivors to this block's global
-// scratch, copied to the new frontier at the end.  L(v) is staged into the shared-memory map when it fits;
+// the shared-memory set (shrinking hi when the set would overflow), checks
+// them and appends the survivors to this block's global scratch, copied to
+// the new frontier at the end.  L(v) is staged into the shared-memory map when it fits;
 // otherwise membership in L(v) is a binary search in its row.
 __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
-                                uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst,
+                                uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst, int* hist,
                                 unsigned long long* cnt) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
@@ -604,26 +665,21 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
     int64_t total_acc = 0;
     uint32_t lo = 0;
     int64_t width = v;
+    uint32_t* hi_sm = reinterpret_cast<uint32_t*>(&sh[SH_HI]);
     while ((int64_t)lo < (int64_t)v) {
-        const uint32_t hi = (uint32_t)min((int64_t)v, (int64_t)lo + width);
         for (int s = tid; s < S_CAP; s += nthr) S[s] = kEmpty;
         if (tid == 0) {
             sh[SH_UNIQ] = 0;
             sh[SH_OVF] = 0;
             sh[SH_ACC] = 0;
             sh[SH_NC] = 0;
+            *hi_sm = (uint32_t)min((int64_t)v, (int64_t)lo + width);
         }
         __syncthreads();
-        gather_block(p, nb, ne, lo, hi, S, log_s, Mp, log_m, limit, &sh[SH_UNIQ], (volatile int*)&sh[SH_OVF],
-                     wsum, sex, sst, cnt[1]);
+        gather_block(p, nb, ne, lo, hi_sm, S, log_s, Mp, log_m, limit, &sh[SH_UNIQ], (volatile int*)&sh[SH_OVF],
+                     wsum, sex, sst, C, hist, &sh[SH_TMP], cnt[1]);
         __syncthreads();
-        const int nS = *(volatile int*)&sh[SH_UNIQ];
-        if (*(volatile int*)&sh[SH_OVF] || nS > limit) {
-            width = (int64_t)(hi - lo) / 2;
-            if (width < 1) width = 1;
-            __syncthreads();
-            continue;
-        }
+        const uint32_t hi = *(volatile uint32_t*)hi_sm;
         // compact the set into C (any order)
         for (int sb = 32 * wid; sb < S_CAP; sb += 32 * nw) {
             const uint32_t h = S[sb + lane];
@@ -678,7 +734,8 @@ __global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
     extern __shared__ uint32_t sm[];
     int* sh = reinterpret_cast<int*>(sm);
     int* wsum = sh + SH_WORDS;                                      // 33 ints (+ pad)
-    int* sex = wsum + 34;                                           // blockDim + 1 ints
+    int* hist = wsum + 34;                                          // 256 ints
+    int* sex = hist + 256;                                          // blockDim + 1 ints
     int64_t* sst = reinterpret_cast<int64_t*>(sex + ((blockDim.x + 2) & ~1u));  // blockDim int64
     uint32_t* S = reinterpret_cast<uint32_t*>(sst + blockDim.x);
     uint32_t* M = S + (1 << p.log_s);
@@ -687,7 +744,7 @@ __global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
     unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int n1 = *p.list_n;
     for (int i = blockIdx.x; i < n1; i += gridDim.x) {
-        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, cnt);
+        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, hist, cnt);
         __syncthreads();
     }
     cnt[1] = warp_sum(cnt[1]);
