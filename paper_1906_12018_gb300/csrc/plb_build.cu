@@ -355,6 +355,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             }
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));
+            if (hctr->guard) return PLB_ERR_CUDA;
             if (!hctr->fovf) break;
             // new-frontier buffer too small: grow it and run the gather again
             const int64_t need = (int64_t)hctr->cursor;

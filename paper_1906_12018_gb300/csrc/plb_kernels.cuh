@@ -31,6 +31,7 @@ struct RoundCounters {
     int nO1_base, nO2_base;       // tier-list sizes made by k_collect (for reruns)
     int fovf;                     // new-frontier buffer overflow
     unsigned int max_dist;        // finalize: largest stored distance
+    int guard;                    // a kernel met a broken capacity invariant (internal error)
 };
 
 struct GpParams {

@@ -519,7 +519,8 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
         }
         if (tid == 0) msgs += total;
         __syncthreads();
-        if (*ovf_sm) {
+        // concurrent inserts can pass the limit without raising the flag
+        if (*ovf_sm || *(volatile int*)cnt_sm > limit) {
             shrink_pass(S, log_s, C, limit, lo, hi_sm, cnt_sm, hist, tmp);
             if (tid == 0) *ovf_sm = 0;
             __syncthreads();
@@ -688,10 +689,14 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
             int base = 0;
             if (lane == 0 && m) base = atomicAdd(&sh[SH_NC], __popc(m));
             base = __shfl_sync(kFull, base, 0);
-            if (has) C[base + __popc(m & ((1u << lane) - 1u))] = h;
+            const int idx = base + __popc(m & ((1u << lane) - 1u));
+            if (has) {
+                if (idx < limit) C[idx] = h;
+                else p.ctr->guard = 1;  // invariant broken: report instead of writing out of bounds
+            }
         }
         __syncthreads();
-        const int nc = *(volatile int*)&sh[SH_NC];
+        const int nc = min(*(volatile int*)&sh[SH_NC], limit);
         if (tid == 0) cnt[2] += nc;
         // distance checks: warp w takes candidate chunks w, w + nw, ...; the
         // survivors are appended (unsorted) to this block's scratch
