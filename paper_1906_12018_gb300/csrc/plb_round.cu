@@ -242,24 +242,32 @@ constexpr int kPrefilterMinItems = 12;  // prefilter only candidates with longer
 // Top-hub witness prefilter for the 32 candidates of a chunk (one per lane):
 // candidate h has a witness among the kTopHubs highest-ranked hubs iff some
 // byte position w has top[v][w] + top[h][w] <= d (saturating byte add; 255 =
-// not a hub).  Each lane holds 8 bytes of v's row (tv0, tv1); the warp tests
-// one candidate per step with one coalesced 256-byte load.  Returns the mask
-// of lanes whose candidate is pruned.
-__device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, uint32_t tv0, uint32_t tv1, uint32_t d,
-                                                  uint32_t h, bool valid) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t dd = d * 0x01010101u;
-    // d <= 254 keeps "absent" (255, saturated) above every threshold
-    unsigned todo = __ballot_sync(kFull, valid && d <= 254u), pruned = 0;
-    while (todo) {
-        const int k = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const uint32_t hk = __shfl_sync(kFull, h, k);
-        const uint2 th = *reinterpret_cast<const uint2*>(top + (int64_t)hk * kTopHubs + 8 * lane);
-        const uint32_t hit = __vcmpleu4(__vaddus4(th.x, tv0), dd) | __vcmpleu4(__vaddus4(th.y, tv1), dd);
-        if (__any_sync(kFull, hit != 0)) pruned |= 1u << k;
+// not a hub).  Each lane tests its own candidate: 16 independent 16-byte
+// loads of h's row against v's row tv (64 words in shared memory, read as
+// broadcasts).  Returns the mask of lanes whose candidate is pruned.
+__device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, const uint32_t* tv, uint32_t d, uint32_t h,
+                                                  bool valid) {
+    valid = valid && d <= 254u;  // d <= 254 keeps "absent" (255, saturated) above every threshold
+    uint32_t hit = 0;
+    if (valid) {
+        const uint32_t dd = d * 0x01010101u;
+        const uint4* th = reinterpret_cast<const uint4*>(top + (int64_t)h * kTopHubs);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint4 a[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = th[8 * half + q];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int w = 4 * (8 * half + q);
+                hit |= __vcmpleu4(__vaddus4(a[q].x, tv[w + 0]), dd);
+                hit |= __vcmpleu4(__vaddus4(a[q].y, tv[w + 1]), dd);
+                hit |= __vcmpleu4(__vaddus4(a[q].z, tv[w + 2]), dd);
+                hit |= __vcmpleu4(__vaddus4(a[q].w, tv[w + 3]), dd);
+            }
+        }
     }
-    return pruned;
+    return __ballot_sync(kFull, hit != 0);
 }
 
 // Distance check of up to 32 candidates held one per lane (valid lanes).
@@ -276,7 +284,7 @@ __device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, uint32_t t
 // whose candidate survives.
 __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_t* M, int log_m, const uint32_t* lv,
                                                 int64_t lvlen, uint32_t h, bool valid, unsigned* pm_sm,
-                                                unsigned long long& probed, uint32_t tv0, uint32_t tv1,
+                                                unsigned long long& probed, const uint32_t* tv,
                                                 unsigned long long& prefiltered) {
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
@@ -297,7 +305,7 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
         }
     }
     // candidates with a long check first try the top-hub prefilter
-    const unsigned pf = top_prefilter(p.top, tv0, tv1, p.d, h, valid && items >= kPrefilterMinItems);
+    const unsigned pf = top_prefilter(p.top, tv, p.d, h, valid && items >= kPrefilterMinItems);
     if (lane == 0) prefiltered += __popc(pf);
     if ((pf >> lane) & 1u) {
         valid = false;
@@ -542,7 +550,8 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
     const int nwarps = blockDim.x >> 5;
     const int S_CAP = 1 << p.log_s, M_CAP = 1 << p.log_m;
     int* wsc = reinterpret_cast<int*>(sm) + wib * 4;  // [0] unique count [1] overflow [3] pruned mask
-    uint32_t* S = sm + 4 * nwarps + wib * (S_CAP + M_CAP);
+    uint32_t* tvs = sm + 4 * nwarps;                   // per warp: v's top-hub row (64 words)
+    uint32_t* S = tvs + nwarps * (kTopHubs / 4) + wib * (S_CAP + M_CAP);
     uint32_t* M = S + S_CAP;
     unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
     unsigned long long c_pref = 0;
@@ -590,14 +599,17 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
         }
         __syncwarp();
         // distance checks, 32 candidates at a time; survivors compacted in place
-        const uint2 tv = *reinterpret_cast<const uint2*>(p.top + (int64_t)v * kTopHubs + 8 * lane);
+        uint32_t* tv = tvs + wib * (kTopHubs / 4);
+        tv[lane] = reinterpret_cast<const uint32_t*>(p.top + (int64_t)v * kTopHubs)[lane];
+        tv[lane + 32] = reinterpret_cast<const uint32_t*>(p.top + (int64_t)v * kTopHubs)[lane + 32];
+        __syncwarp();
         int nacc = 0;
         for (int cb = 0; cb < nc; cb += 32) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
             const unsigned okm = check_chunk(p, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3], c_probed,
-                                             tv.x, tv.y, c_pref);
+                                             tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
@@ -640,7 +652,7 @@ enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_HI = 4, SH_TMP = 5, SH
 // the new frontier at the end.  L(v) is staged into the shared-memory map when it fits;
 // otherwise membership in L(v) is a binary search in its row.
 __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
-                                uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst, int* hist,
+                                uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst, int* hist, uint32_t* tv,
                                 unsigned long long* cnt) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
@@ -662,7 +674,7 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
         cnt[3] += ll;
         cnt[6] += 1;
     }
-    const uint2 tv = *reinterpret_cast<const uint2*>(p.top + (int64_t)v * kTopHubs + 8 * lane);
+    if (tid < kTopHubs / 4) tv[tid] = reinterpret_cast<const uint32_t*>(p.top + (int64_t)v * kTopHubs)[tid];
     int64_t total_acc = 0;
     uint32_t lo = 0;
     int64_t width = v;
@@ -705,7 +717,7 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
             const uint32_t h = valid ? C[cb + lane] : 0u;
             if (!useM && valid && row_find(lv, ll, h) != kEmpty) valid = false;  // already a hub of v
             const unsigned okm = check_chunk(p, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4],
-                                             tv.x, tv.y, cnt[7]);
+                                             tv, cnt[7]);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
             base = __shfl_sync(kFull, base, 0);
@@ -735,12 +747,13 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
+__global__ void __launch_bounds__(512, 1) k_gp_block(GpParams p) {
     extern __shared__ uint32_t sm[];
     int* sh = reinterpret_cast<int*>(sm);
     int* wsum = sh + SH_WORDS;                                      // 33 ints (+ pad)
     int* hist = wsum + 34;                                          // 256 ints
-    int* sex = hist + 256;                                          // blockDim + 1 ints
+    uint32_t* tv = reinterpret_cast<uint32_t*>(hist + 256);         // v's top-hub row: 64 words
+    int* sex = reinterpret_cast<int*>(tv + kTopHubs / 4);           // blockDim + 1 ints
     int64_t* sst = reinterpret_cast<int64_t*>(sex + ((blockDim.x + 2) & ~1u));  // blockDim int64
     uint32_t* S = reinterpret_cast<uint32_t*>(sst + blockDim.x);
     uint32_t* M = S + (1 << p.log_s);
@@ -749,7 +762,7 @@ __global__ void __launch_bounds__(512) k_gp_block(GpParams p) {
     unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int n1 = *p.list_n;
     for (int i = blockIdx.x; i < n1; i += gridDim.x) {
-        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, hist, cnt);
+        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, hist, tv, cnt);
         __syncthreads();
     }
     cnt[1] = warp_sum(cnt[1]);
