@@ -202,7 +202,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int64_t T = n;  // labels so far
     int cur = 0;    // index of current L and previous frontier
     // top-hub distance rows (witness prefilter), updated by each merge
-    uint8_t* top = pool.alloc<uint8_t>(n * kTopHubs);
+    uint32_t* top = pool.alloc<uint32_t>(n * kTopRow);
     PLB_ALLOC_OK();
     k_top_init<<<flat_grid_cap, kFlatThreads, 0, s>>>(top, n);
     // probe index of L (hub-keyed table per long row), rebuilt after each merge
@@ -239,13 +239,13 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     const int w_log_m = ceil_log2_i64(2 * warp_label);
     const int warps_per_block = kGpWarpThreads / 32;
     const size_t w_smem = sizeof(uint32_t) * (4 * warps_per_block +
-                                              (size_t)warps_per_block * (64 + (1 << w_log_s) + (1 << w_log_m)));
+                                              (size_t)warps_per_block * (kTopRow + (1 << w_log_s) + (1 << w_log_m)));
     const int bthr = std::min(512, std::max(64, (o.block_threads / 32) * 32));
     const int block_cand = pow2_at_least(std::max(bthr, o.block_cand_cap));
     const int b_log_s = ceil_log2_i64(2 * (int64_t)block_cand);
     const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);
     // scalars (48) + warp sums (34) + prefix per thread + 64-bit row start per thread + tables
-    const size_t b_smem = sizeof(uint32_t) * (48 + 34 + 256 + 64 + (size_t)((bthr + 2) & ~1) + 2 * (size_t)bthr +
+    const size_t b_smem = sizeof(uint32_t) * (48 + 34 + 256 + kTopRow + (size_t)((bthr + 2) & ~1) + 2 * (size_t)bthr +
                                               (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) + block_cand);
     TierLimits lim;
     lim.warp_bound = 2 * (int64_t)warp_cand;

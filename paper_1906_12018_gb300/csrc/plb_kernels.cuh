@@ -56,13 +56,19 @@ struct GpParams {
     int64_t gscratch_words;    // words per block
     const int64_t* hoff;       // probe index of L: per row a hub-keyed table (empty rows: none)
     const uint32_t* htab;
-    const uint8_t* top;        // per vertex: d(w, x) for the kTopHubs highest-ranked hubs w (255: not a hub)
+    const uint32_t* top;       // per vertex: top-hub masks by distance level (see kTopHubs)
 };
 
-// Witness prefilter: every vertex keeps the label distances of the top-ranked
-// kTopHubs hubs as a byte row, so the label test restricted to those hubs is
-// a handful of byte-SIMD operations (exact: a hit is a real witness).
+// Witness prefilter: for the kTopHubs highest-ranked hubs, every vertex x
+// keeps kTopLevels bitmasks C_t(x) = {w : w in L(x), d(w, x) <= t}, t = 1..
+// kTopLevels (8 words each).  A candidate h at round d has a witness among
+// those hubs when E_i(v) & C_{d-i}(h) != 0 for some i, E_i = C_i & ~C_{i-1}:
+// the label test restricted to those hubs and distances (exact: a hit is a
+// real witness).
 constexpr int kTopHubs = 256;
+constexpr int kTopWords = kTopHubs / 32;             // words per mask
+constexpr int kTopLevels = 7;                        // distance levels 1..7
+constexpr int kTopRow = kTopLevels * kTopWords;      // words per vertex
 
 // Rows of L with at least this many entries get a hub-keyed probe table.
 constexpr int kIndexMinLen = 16;

@@ -240,34 +240,38 @@ __device__ __forceinline__ uint32_t row_find(const uint32_t* r, int64_t len, uin
 constexpr int kPrefilterMinItems = 12;  // prefilter only candidates with longer checks
 
 // Top-hub witness prefilter for the 32 candidates of a chunk (one per lane):
-// candidate h has a witness among the kTopHubs highest-ranked hubs iff some
-// byte position w has top[v][w] + top[h][w] <= d (saturating byte add; 255 =
-// not a hub).  Each lane tests its own candidate: 16 independent 16-byte
-// loads of h's row against v's row tv (64 words in shared memory, read as
-// broadcasts).  Returns the mask of lanes whose candidate is pruned.
-__device__ __forceinline__ unsigned top_prefilter(const uint8_t* top, const uint32_t* tv, uint32_t d, uint32_t h,
+// candidate h has a witness among the kTopHubs highest-ranked hubs when
+// E_i(v) & C_j(h) != 0 for some i >= 1, j = min(d - i, kTopLevels) >= 1, where
+// E_i(v) (v's hubs at distance exactly i) is staged in shared memory (ev,
+// kTopLevels x kTopWords words) and C_j(h) is h's cumulative mask.  Returns
+// the mask of lanes whose candidate is pruned.
+__device__ __forceinline__ unsigned top_prefilter(const uint32_t* top, const uint32_t* ev, uint32_t d, uint32_t h,
                                                   bool valid) {
-    valid = valid && d <= 254u;  // d <= 254 keeps "absent" (255, saturated) above every threshold
     uint32_t hit = 0;
     if (valid) {
-        const uint32_t dd = d * 0x01010101u;
-        const uint4* th = reinterpret_cast<const uint4*>(top + (int64_t)h * kTopHubs);
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            uint4 a[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) a[q] = th[8 * half + q];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int w = 4 * (8 * half + q);
-                hit |= __vcmpleu4(__vaddus4(a[q].x, tv[w + 0]), dd);
-                hit |= __vcmpleu4(__vaddus4(a[q].y, tv[w + 1]), dd);
-                hit |= __vcmpleu4(__vaddus4(a[q].z, tv[w + 2]), dd);
-                hit |= __vcmpleu4(__vaddus4(a[q].w, tv[w + 3]), dd);
-            }
+        const uint32_t* th = top + (int64_t)h * kTopRow;
+        const int imax = min((int)d - 1, kTopLevels);
+        for (int i = 1; i <= imax; ++i) {
+            const int j = min((int)d - i, kTopLevels);
+            const uint4* cj = reinterpret_cast<const uint4*>(th + (j - 1) * kTopWords);
+            const uint4 a = cj[0], b = cj[1];
+            const uint32_t* e = ev + (i - 1) * kTopWords;
+            hit |= (a.x & e[0]) | (a.y & e[1]) | (a.z & e[2]) | (a.w & e[3]) | (b.x & e[4]) | (b.y & e[5]) |
+                   (b.z & e[6]) | (b.w & e[7]);
         }
     }
     return __ballot_sync(kFull, hit != 0);
+}
+
+// Stage E_i(v) = C_i(v) & ~C_{i-1}(v), i = 1..kTopLevels, into ev (cooperative:
+// thread t of nthr handles words t, t + nthr, ...).
+__device__ __forceinline__ void stage_exact_levels(const uint32_t* top, int32_t v, uint32_t* ev, int t, int nthr) {
+    const uint32_t* tv = top + (int64_t)v * kTopRow;
+    for (int q = t; q < kTopRow; q += nthr) {
+        const uint32_t c = tv[q];
+        const uint32_t prev = q >= kTopWords ? tv[q - kTopWords] : 0u;
+        ev[q] = c & ~prev;
+    }
 }
 
 // Distance check of up to 32 candidates held one per lane (valid lanes).
@@ -544,14 +548,14 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
 //  3. compact S in place and check the candidates 32 at a time;
 //  4. append the accepted hubs (unsorted) to the new frontier.
 // A vertex whose unique candidates exceed cand_limit goes to the block tier.
-__global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
+__global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
     extern __shared__ uint32_t sm[];
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int S_CAP = 1 << p.log_s, M_CAP = 1 << p.log_m;
     int* wsc = reinterpret_cast<int*>(sm) + wib * 4;  // [0] unique count [1] overflow [3] pruned mask
-    uint32_t* tvs = sm + 4 * nwarps;                   // per warp: v's top-hub row (64 words)
-    uint32_t* S = tvs + nwarps * (kTopHubs / 4) + wib * (S_CAP + M_CAP);
+    uint32_t* tvs = sm + 4 * nwarps;                   // per warp: v's exact-distance top-hub masks
+    uint32_t* S = tvs + nwarps * kTopRow + wib * (S_CAP + M_CAP);
     uint32_t* M = S + S_CAP;
     unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
     unsigned long long c_pref = 0;
@@ -599,9 +603,8 @@ __global__ void __launch_bounds__(256) k_gp_warp(GpParams p) {
         }
         __syncwarp();
         // distance checks, 32 candidates at a time; survivors compacted in place
-        uint32_t* tv = tvs + wib * (kTopHubs / 4);
-        tv[lane] = reinterpret_cast<const uint32_t*>(p.top + (int64_t)v * kTopHubs)[lane];
-        tv[lane + 32] = reinterpret_cast<const uint32_t*>(p.top + (int64_t)v * kTopHubs)[lane + 32];
+        uint32_t* tv = tvs + wib * kTopRow;
+        stage_exact_levels(p.top, v, tv, lane, 32);
         __syncwarp();
         int nacc = 0;
         for (int cb = 0; cb < nc; cb += 32) {
@@ -674,7 +677,7 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
         cnt[3] += ll;
         cnt[6] += 1;
     }
-    if (tid < kTopHubs / 4) tv[tid] = reinterpret_cast<const uint32_t*>(p.top + (int64_t)v * kTopHubs)[tid];
+    stage_exact_levels(p.top, v, tv, tid, nthr);
     int64_t total_acc = 0;
     uint32_t lo = 0;
     int64_t width = v;
@@ -752,8 +755,8 @@ __global__ void __launch_bounds__(512, 1) k_gp_block(GpParams p) {
     int* sh = reinterpret_cast<int*>(sm);
     int* wsum = sh + SH_WORDS;                                      // 33 ints (+ pad)
     int* hist = wsum + 34;                                          // 256 ints
-    uint32_t* tv = reinterpret_cast<uint32_t*>(hist + 256);         // v's top-hub row: 64 words
-    int* sex = reinterpret_cast<int*>(tv + kTopHubs / 4);           // blockDim + 1 ints
+    uint32_t* tv = reinterpret_cast<uint32_t*>(hist + 256);         // v's exact-distance top-hub masks
+    int* sex = reinterpret_cast<int*>(tv + kTopRow);                // blockDim + 1 ints
     int64_t* sst = reinterpret_cast<int64_t*>(sex + ((blockDim.x + 2) & ~1u));  // blockDim int64
     uint32_t* S = reinterpret_cast<uint32_t*>(sst + blockDim.x);
     uint32_t* M = S + (1 << p.log_s);
@@ -981,7 +984,7 @@ __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int
 // New entries (dist d) of each active vertex: warp per vertex.
 __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
                             const uint64_t* fse_new, const uint32_t* fhub_new, const int32_t* A,
-                            const RoundCounters* ctr, uint32_t d, uint8_t* top) {
+                            const RoundCounters* ctr, uint32_t d, uint32_t* top) {
     const int nA = ctr->nA;
     const int lane = lane_id();
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -995,21 +998,21 @@ __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int
             const uint32_t h = fr[j];
             const int64_t pos = loff_new[v] + j + lower_bound_u32(lent + ob, ol, pack(h, 0));
             lent_new[pos] = pack(h, d);
-            if (h < (uint32_t)kTopHubs) top[(int64_t)v * kTopHubs + h] = (uint8_t)d;
+            if (h < (uint32_t)kTopHubs && d <= (uint32_t)kTopLevels) {
+                uint32_t* tv = top + (int64_t)v * kTopRow + (h >> 5);
+                for (int t = (int)d; t <= kTopLevels; ++t) atomicOr(tv + (t - 1) * kTopWords, 1u << (h & 31));
+            }
         }
     }
 }
 
-// top[x][w] = 255 except top[w][w] = 0 for w < kTopHubs (the self labels).
-__global__ void k_top_init(uint8_t* top, int64_t n) {
-    const int64_t words = n * (kTopHubs / 4);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t x = i / (kTopHubs / 4), w0 = (i % (kTopHubs / 4)) * 4;
-        uint32_t word = 0xFFFFFFFFu;
-        if (x >= w0 && x < w0 + 4 && x < kTopHubs) word &= ~(0xFFu << (8 * (x - w0)));
-        reinterpret_cast<uint32_t*>(top)[i] = word;
-    }
+// Masks start empty (distance-0 self labels are not part of any level).
+__global__ void k_top_init(uint32_t* top, int64_t n) {
+    const int64_t words = n * kTopRow;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+        top[i] = 0u;
 }
+
 
 // ------------------------------------------------------------ finalize
 __global__ void k_final_len(const int64_t* loff, const int32_t* inv, int64_t n, int64_t* len) {

@@ -41,8 +41,8 @@ __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int
                             const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n);
 __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
                             const uint64_t* fse_new, const uint32_t* fhub_new, const int32_t* A,
-                            const RoundCounters* ctr, uint32_t d, uint8_t* top);
-__global__ void k_top_init(uint8_t* top, int64_t n);
+                            const RoundCounters* ctr, uint32_t d, uint32_t* top);
+__global__ void k_top_init(uint32_t* top, int64_t n);
 __global__ void k_final_len(const int64_t* loff, const int32_t* inv, int64_t n, int64_t* len);
 __global__ void k_finalize(const int64_t* loff, const uint32_t* lent, const int32_t* inv, const int64_t* out_off,
                            uint32_t* out_packed, uint32_t* out_hub, uint8_t* out_dist, int64_t n,
