@@ -74,8 +74,11 @@ typedef struct {
     int32_t block_label_cap;   /* largest |L(v)| handled one-vertex-per-block in shared memory */
     int32_t block_cand_cap;    /* largest candidate count for the block tier */
     int32_t block_threads;     /* threads of the block tier (multiple of 32, <= 1024) */
-    int32_t use_graph;         /* 1: run the round loop as a captured CUDA graph with a
-                                  device-side while condition (no per-round host sync) */
+    int32_t use_graph;         /* 1: run the round loop as ONE captured CUDA graph with a
+                                  device-side while condition (no per-round host sync);
+                                  buffers get fixed capacities (32 labels per vertex, at
+                                  least 2^20); a round that would exceed them is redone
+                                  host-driven.  Default 0 (plb_build_batch without options: 1) */
     int32_t profile;           /* 1: time each kernel class with CUDA events */
     int32_t reserved[8];
 } plb_options;

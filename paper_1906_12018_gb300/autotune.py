@@ -7,7 +7,8 @@ Knobs (``plb_options``):
   * warp_label_cap  |L(v)| the warp tier stages in its shared-memory map (the
                     shared-memory probe width of the warp tier);
   * block_threads   threads of the block tier;
-  * block_cand_cap  candidates per hub-range pass of the block tier.
+  * block_cand_cap  candidates per hub-range pass of the block tier;
+  * use_graph       round loop as one captured CUDA graph (1) or host-driven (0).
 
 Coordinate descent from the defaults: each knob in turn takes the value with
 the smallest measured build time on a sample of the workload (other knobs
@@ -22,6 +23,7 @@ import os
 import time
 
 SPACE = {
+    "use_graph": [1, 0],
     "warp_cand_cap": [256, 512, 1024],
     "warp_label_cap": [256, 512, 1024],
     "block_threads": [256, 512],
@@ -82,6 +84,8 @@ def tune_batch(sample, space: dict | None = None, reps: int = 2, use_cache: bool
     if use_cache and key in cache:
         return plb.default_options(**cache[key]["options"]), {"key": key, "cached": True, **cache[key]}
     cur = {k: int(getattr(plb.default_options(), k)) for k in space}
+    if "use_graph" in space:
+        cur["use_graph"] = space["use_graph"][0]
     _time_batch(sample, plb.default_options(**cur), 1)  # warm-up
     base = _time_batch(sample, plb.default_options(**cur), reps)
     best_t, trials = base, 1

@@ -267,7 +267,12 @@ int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k, 
     if (k == 0) return PLB_OK;
     if (k > (1 << 24)) return PLB_ERR_TOO_LARGE;
     plb_options o;
-    if (opt) o = *opt; else plb_default_options(&o);
+    if (opt) {
+        o = *opt;
+    } else {
+        plb_default_options(&o);
+        o.use_graph = 1;  // many small graphs: the round loop runs as one captured graph
+    }
     if (!sane_options(o)) return PLB_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     (void)cudaGetLastError();

@@ -219,10 +219,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             htab = pool.alloc<uint32_t>(hcap);
             if (pool.failed) return PLB_ERR_OOM;
         }
-        k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[which], n, tmp64);
+        k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[which], n, tmp64, ctr);
         if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
         k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t), s>>>(
-            loff[which], lent[which], hoff, htab, n);
+            loff[which], lent[which], hoff, htab, n, ctr);
         st.launches += 4;
         return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
     };
@@ -273,21 +273,222 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     PLB_ALLOC_OK();
 
     // ------------------------------------------------------------ rounds
+    // launch sequences of one round (buffers of parity c -> x = c ^ 1)
+    auto gp_params = [&](int c, int x, int64_t fc) {
+        GpParams p{};
+        p.roff = roff;
+        p.rcol = rcol;
+        p.loff = loff[c];
+        p.lent = lent[c];
+        p.fse = fse[c];
+        p.fhub = fhub[c];
+        p.fse_new = fse[x];
+        p.fhub_new = fhub[x];
+        p.fcap = (unsigned long long)fc;
+        p.ctr = ctr;
+        p.hoff = hoff;
+        p.htab = htab;
+        p.top = top;
+        p.gscratch = gacc;
+        p.gscratch_words = std::max<int64_t>(n, 1);
+        return p;
+    };
+    auto launch_frontier = [&](int c, int x) -> cudaError_t {
+        k_active_degree<<<gflat, kFlatThreads, 0, s>>>(roff, A, ctr, tmp64, n);
+        cudaError_t e = exclusive_scan_i64(tmp64, aoff, n, scan_scr, s);
+        if (e != cudaSuccess) return e;
+        k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[c], fhub[c], A, aoff, ctr, recv, n);
+        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[c], n, fse[x], R, O1, ctr, lim);
+        k_after_collect<<<1, 1, 0, s>>>(ctr);
+        st.launches += 7;
+        return cudaGetLastError();
+    };
+    auto launch_gp = [&](GpParams p, cudaEvent_t* g1) -> cudaError_t {
+        p.list = R;  // warp tier
+        p.list_n = &ctr->nR;
+        p.esc = O1;
+        p.esc_n = &ctr->nO1;
+        p.log_s = w_log_s;
+        p.log_m = w_log_m;
+        p.cand_limit = warp_cand;
+        k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
+        if (g1) *g1 = tm.mark();
+        p.list = O1;  // block tier (never escalates)
+        p.list_n = &ctr->nO1;
+        p.esc = nullptr;
+        p.esc_n = nullptr;
+        p.log_s = b_log_s;
+        p.log_m = b_log_m;
+        p.cand_limit = block_cand;
+        k_gp_block<<<grid_b, bthr, b_smem, s>>>(p);
+        st.launches += 2;
+        return cudaGetLastError();
+    };
+    auto launch_merge = [&](int c, int x) -> cudaError_t {
+        k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[c], fse[x], n, tmp64, A, ctr);
+        // sort the new frontier rows (appended unsorted by the gather/prune kernels)
+        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[x], fhub[x], A, ctr, big, giant);
+        k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(fse[x], fhub[x], big, &ctr->nBig, nullptr,
+                                                                        0, ctr);
+        k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[x], fhub[x], giant, &ctr->nGiant,
+                                                                            sortscr, sort_words, ctr);
+        cudaError_t e = exclusive_scan_i64(tmp64, loff[x], n, scan_scr, s);
+        if (e != cudaSuccess) return e;
+        k_merge_old<<<flat_grid_cap, kFlatThreads, 0, s>>>(loff[c], lent[c], loff[x], lent[x], fse[x], fhub[x], n,
+                                                           ctr);
+        k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
+            loff[c], lent[c], loff[x], lent[x], fse[x], fhub[x], A, ctr, top);
+        st.launches += 9;
+        return cudaGetLastError();
+    };
+
     int status = PLB_OK;
-    int d = 0;
+    int d = 0;          // last completed round
+    bool finished = false;
     std::vector<std::pair<int, cudaEvent_t>> round_ev;  // (round, start event)
-    for (;;) {
+
+    // ---- graph mode: the whole round loop as one CUDA graph with a device-side
+    // while condition (two rounds per body: the buffer parities alternate)
+    if (o.use_graph) {
+        const int64_t lc = std::max<int64_t>(std::max<int64_t>(32 * n, T + 1024), 1 << 20);
+        auto grow = [&](uint32_t*& buf, int64_t& cap, int64_t want, int64_t keep) -> bool {
+            if (cap >= want) return true;
+            uint32_t* nb = pool.alloc<uint32_t>(want);
+            if (pool.failed) return false;
+            if (keep > 0 && cudaMemcpyAsync(nb, buf, sizeof(uint32_t) * keep, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return false;
+            pool.release(buf);
+            buf = nb;
+            cap = want;
+            return true;
+        };
+        for (int b = 0; b < 2; ++b) {
+            if (!grow(lent[b], lcap[b], lc, b == cur ? T : 0) || !grow(fhub[b], fcap[b], lc, b == cur ? n : 0))
+                return PLB_ERR_OOM;
+        }
+        if (!grow(htab, hcap, 4 * lc, 0)) return PLB_ERR_OOM;
+        {
+            const int e = build_index(cur, T);  // the index of the current labels in the grown table
+            if (e != PLB_OK) return e;
+        }
+        RoundStat* dstat = pool.alloc<RoundStat>(PLB_MAX_ROUNDS);
+        PLB_ALLOC_OK();
+        PLB_CK(cudaMemsetAsync(dstat, 0, sizeof(RoundStat) * PLB_MAX_ROUNDS, s));
+        PLB_CK(cudaStreamSynchronize(s));
+        hctr->T = T;
+        hctr->lcap = lc;
+        hctr->fcap = lc;
+        hctr->hcap = 4 * lc;
+        hctr->cur = cur;
+        PLB_CK(cudaMemcpyAsync(&ctr->cur, &hctr->cur, sizeof(int), cudaMemcpyHostToDevice, s));
+        PLB_CK(cudaMemcpyAsync(&ctr->T, &hctr->T, 4 * sizeof(long long), cudaMemcpyHostToDevice, s));
+        cudaEvent_t ga = tm.on ? tm.mark() : nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        struct GraphGuard {
+            cudaGraph_t* g;
+            cudaGraphExec_t* e;
+            ~GraphGuard() {
+                if (*e) cudaGraphExecDestroy(*e);
+                if (*g) cudaGraphDestroy(*g);
+            }
+        } gguard{&graph, &exec};
+        PLB_CK(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle handle;
+        PLB_CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        PLB_CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        PLB_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        const int64_t launches0 = st.launches;
+        for (int r = 0; r < 2 && ce == cudaSuccess; ++r) {
+            const int c = cur ^ r, x = c ^ 1;
+            k_g_begin<<<1, 1, 0, s>>>(ctr);
+            ce = launch_frontier(c, x);
+            if (ce == cudaSuccess) ce = launch_gp(gp_params(c, x, lc), nullptr);
+            if (ce == cudaSuccess) {
+                k_g_check<<<1, 1, 0, s>>>(ctr, dstat);
+                ce = launch_merge(c, x);
+            }
+            if (ce == cudaSuccess) {
+                k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[x], n, tmp64, ctr);
+                ce = exclusive_scan_i64(tmp64, hoff, n, scan_scr, s);
+            }
+            if (ce == cudaSuccess) {
+                k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t), s>>>(
+                    loff[x], lent[x], hoff, htab, n, ctr);
+                k_g_finish<<<1, 1, 0, s>>>(ctr);
+                ce = cudaGetLastError();
+            }
+        }
+        k_g_cond<<<1, 1, 0, s>>>(ctr, handle);
+        const cudaError_t ee = cudaStreamEndCapture(s, &body);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            (void)cudaGetLastError();
+            return PLB_ERR_CUDA;
+        }
+        const int64_t per_pair = st.launches - launches0 + 1;
+        st.launches = launches0;
+        PLB_CK(cudaGraphInstantiate(&exec, graph, 0));
+        PLB_CK(cudaGraphLaunch(exec, s));
+        PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+        std::vector<RoundStat> hstat(PLB_MAX_ROUNDS);
+        PLB_CK(cudaMemcpyAsync(hstat.data(), dstat, sizeof(RoundStat) * PLB_MAX_ROUNDS, cudaMemcpyDeviceToHost, s));
+        PLB_CK(cudaStreamSynchronize(s));
+        if (tm.on) tm.span(T_GPW, ga, tm.mark());
+        if (hctr->guard) return PLB_ERR_CUDA;
+        const int dd = (int)hctr->d;  // last round started
+        st.launches += per_pair * ((dd + 1) / 2);
+        for (int r = 1; r <= dd && r < PLB_MAX_ROUNDS; ++r) {
+            const RoundStat& x = hstat[r];
+            st.receivers[r] = x.receivers;
+            st.accepted[r] = x.accepted;
+            st.unique_round[r] = x.uniq;
+            st.prefiltered_round[r] = x.pref;
+            st.probed_round[r] = x.probed;
+            st.messages_round[r] = x.msgs;
+            st.arcs_scanned += x.arcs;
+            st.messages += x.msgs;
+            st.unique_candidates += x.uniq;
+            st.staged_entries += x.staged;
+            st.probed_entries += x.probed;
+            st.tier_vertices[0] += x.tier0;
+            st.tier_vertices[1] += x.tier1;
+        }
+        T = hctr->T;
+        cur = hctr->cur;
+        if (hctr->err) return hctr->err;
+        if (!hctr->fallback) {
+            d = dd;
+            finished = true;
+        } else {
+            // a capacity was exceeded in round dd: redo it on the host
+            d = dd - 1;
+            st.receivers[dd] = st.accepted[dd] = st.unique_round[dd] = 0;
+            hctr->nA = hctr->nA_saved;
+            PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
+            PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
+            PLB_CK(cudaMemcpyAsync(&ctr->nA, &hctr->nA, sizeof(int), cudaMemcpyHostToDevice, s));
+            PLB_CK(cudaMemsetAsync(&ctr->done, 0, sizeof(int) * 2, s));
+            st.reruns += 1;
+            // the index in htab is that of L[cur] (the round stopped before the merge)
+        }
+    }
+
+    // ---- host-driven rounds (from round d + 1)
+    while (!finished) {
         ++d;
         const int nxt = cur ^ 1;
         cudaEvent_t r0 = tm.on ? tm.mark() : nullptr;
+        k_set_round<<<1, 1, 0, s>>>(ctr, (uint32_t)d);
         // frontier: mark receivers from the active list, collect them
-        k_active_degree<<<gflat, kFlatThreads, 0, s>>>(roff, A, ctr, tmp64, n);
-        PLB_CK(exclusive_scan_i64(tmp64, aoff, n, scan_scr, s));
-        k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[cur], fhub[cur], A, aoff, ctr, recv, n);
-        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse[nxt], R, O1, ctr, lim);
-        k_after_collect<<<1, 1, 0, s>>>(ctr);
-        PLB_CK(cudaGetLastError());
-        st.launches += 5;
+        PLB_CK(launch_frontier(cur, nxt));
         // size the new frontier buffer from the candidate bound (no re-run)
         PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
         PLB_CK(cudaStreamSynchronize(s));
@@ -305,50 +506,13 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         if (tm.on) tm.span(T_FRONT, r0, r1);
         bool rerun = false;
         for (;;) {
-            GpParams p{};
-            p.roff = roff;
-            p.rcol = rcol;
-            p.loff = loff[cur];
-            p.lent = lent[cur];
-            p.fse = fse[cur];
-            p.fhub = fhub[cur];
-            p.fse_new = fse[nxt];
-            p.fhub_new = fhub[nxt];
-            p.fcap = (unsigned long long)fcap[nxt];
-            p.ctr = ctr;
-            p.d = (uint32_t)d;
-            p.hoff = hoff;
-            p.htab = htab;
-            p.top = top;
             if (rerun) {
                 k_rerun_reset<<<gflat, kFlatThreads, 0, s>>>(ctr, fse[nxt], n);
                 st.launches += 1;
             }
-            cudaEvent_t g0 = tm.on ? tm.mark() : nullptr;
-            // warp tier
-            p.list = R;
-            p.list_n = &ctr->nR;
-            p.esc = O1;
-            p.esc_n = &ctr->nO1;
-            p.log_s = w_log_s;
-            p.log_m = w_log_m;
-            p.cand_limit = warp_cand;
-            k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
-            cudaEvent_t g1 = tm.on ? tm.mark() : nullptr;
-            // block tier (never escalates)
-            p.list = O1;
-            p.list_n = &ctr->nO1;
-            p.esc = nullptr;
-            p.esc_n = nullptr;
-            p.log_s = b_log_s;
-            p.log_m = b_log_m;
-            p.cand_limit = block_cand;
-            p.gscratch = gacc;
-            p.gscratch_words = std::max<int64_t>(n, 1);
-            k_gp_block<<<grid_b, bthr, b_smem, s>>>(p);
+            cudaEvent_t g0 = tm.on ? tm.mark() : nullptr, g1 = nullptr;
+            PLB_CK(launch_gp(gp_params(cur, nxt, fcap[nxt]), tm.on ? &g1 : nullptr));
             cudaEvent_t g2 = tm.on ? tm.mark() : nullptr;
-            PLB_CK(cudaGetLastError());
-            st.launches += 2;
             if (tm.on) {
                 tm.span(T_GPW, g0, g1);
                 tm.span(T_GPB, g1, g2);
@@ -396,20 +560,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             lent[nxt] = pool.alloc<uint32_t>(lcap[nxt]);
             PLB_ALLOC_OK();
         }
-        k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[cur], fse[nxt], n, tmp64, A, ctr);
-        // sort the new frontier rows (appended unsorted by the gather/prune kernels)
-        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[nxt], fhub[nxt], A, ctr, big, giant);
-        k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(fse[nxt], fhub[nxt], big, &ctr->nBig,
-                                                                        nullptr, 0);
-        k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[nxt], fhub[nxt], giant,
-                                                                            &ctr->nGiant, sortscr, sort_words);
-        PLB_CK(exclusive_scan_i64(tmp64, loff[nxt], n, scan_scr, s));
-        k_merge_old<<<grid_for((T + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(
-            loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], n);
-        k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
-            loff[cur], lent[cur], loff[nxt], lent[nxt], fse[nxt], fhub[nxt], A, ctr, (uint32_t)d, top);
-        PLB_CK(cudaGetLastError());
-        st.launches += 9;
+        PLB_CK(launch_merge(cur, nxt));
         T = Tn;
         cur = nxt;
         {

@@ -32,6 +32,20 @@ struct RoundCounters {
     int fovf;                     // new-frontier buffer overflow
     unsigned int max_dist;        // finalize: largest stored distance
     int guard;                    // a kernel met a broken capacity invariant (internal error)
+    // loop control (kept across rounds)
+    unsigned int d;               // current round (distance of the labels being accepted)
+    int done;                     // no further round runs; round kernels return at once
+    int fallback;                 // graph mode stopped at a capacity limit: resume on the host
+    int err;                      // status set by the device (PLB_ERR_DIST_OVERFLOW)
+    int nA_saved;                 // active count of the current round (restored on fallback)
+    int cur;                      // buffer parity holding L and the previous frontier
+    long long T;                  // labels so far (graph mode)
+    long long lcap, fcap, hcap;   // buffer capacities (graph mode)
+};
+
+// Per-round statistics written on the device (graph mode).
+struct RoundStat {
+    long long receivers, accepted, uniq, probed, msgs, pref, arcs, staged, tier0, tier1;
 };
 
 struct GpParams {
@@ -48,8 +62,7 @@ struct GpParams {
     const int* list_n;
     int32_t* esc;              // escalation list (next tier)
     int* esc_n;
-    RoundCounters* ctr;
-    uint32_t d;                // round = distance of accepted labels
+    RoundCounters* ctr;        // also holds the round number d (ctr->d)
     int log_s, log_m;          // table sizes (log2 slots): candidate set, L(v) map (block tier: largest)
     int cand_limit;            // max unique candidates per pass (power of two)
     uint32_t* gscratch;        // block tier: per-block buffer of accepted hubs

@@ -131,6 +131,7 @@ __global__ void k_init(const int64_t* roff, int64_t n, int64_t* loff, uint32_t* 
 // adeg[i] = degree of active vertex A[i] (0 beyond nA), for the flat mark.
 __global__ void k_active_degree(const int64_t* roff, const int32_t* A, const RoundCounters* ctr, int64_t* adeg,
                                 int64_t n) {
+    if (ctr->done) return;
     const int nA = ctr->nA;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t x = 0;
@@ -149,6 +150,7 @@ __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t*
                        const int32_t* A, const int64_t* aoff, const RoundCounters* ctr, unsigned long long* recv,
                        int64_t n) {
     __shared__ int64_t sh_r[2];
+    if (ctr->done) return;
     const int64_t nA = ctr->nA;
     if (nA == 0) return;
     const int64_t total = aoff[n];
@@ -175,6 +177,7 @@ __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t*
 // Also clears recv and the new frontier descriptors, and sums the bounds.
 __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const int64_t* loff, int64_t n,
                           uint64_t* fse_new, int32_t* R, int32_t* O1, RoundCounters* ctr, TierLimits lim) {
+    if (ctr->done) return;
     unsigned long long bsum = 0;
     const int lane = lane_id();
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
@@ -209,8 +212,10 @@ __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const i
 }
 
 __global__ void k_after_collect(RoundCounters* ctr) {
+    if (ctr->done) return;
     ctr->nO1_base = ctr->nO1;
     ctr->nO2_base = ctr->nO2;
+    ctr->nA_saved = ctr->nA;
     ctr->nA = 0;
 }
 
@@ -286,9 +291,9 @@ __device__ __forceinline__ void stage_exact_levels(const uint32_t* top, int32_t 
 // All (candidate, entry) pairs are spread over the lanes; a candidate's
 // remaining entries are skipped once it has a witness.  Returns the lanes
 // whose candidate survives.
-__device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_t* M, int log_m, const uint32_t* lv,
-                                                int64_t lvlen, uint32_t h, bool valid, unsigned* pm_sm,
-                                                unsigned long long& probed, const uint32_t* tv,
+__device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, const uint32_t* M, int log_m,
+                                                const uint32_t* lv, int64_t lvlen, uint32_t h, bool valid,
+                                                unsigned* pm_sm, unsigned long long& probed, const uint32_t* tv,
                                                 unsigned long long& prefiltered) {
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
@@ -309,7 +314,7 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
         }
     }
     // candidates with a long check first try the top-hub prefilter
-    const unsigned pf = top_prefilter(p.top, tv, p.d, h, valid && items >= kPrefilterMinItems);
+    const unsigned pf = top_prefilter(p.top, tv, d, h, valid && items >= kPrefilterMinItems);
     if (lane == 0) prefiltered += __popc(pf);
     if ((pf >> lane) & 1u) {
         valid = false;
@@ -335,11 +340,11 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, const uint32_
             if (mk == 0) {
                 const uint32_t x = p.lent[bk + j];
                 const uint32_t dv = M ? map_find(M, log_m, hub_of(x)) : row_find(lv, lvlen, hub_of(x));
-                hit = dv != kEmpty && dv + dist_of(x) <= p.d;
+                hit = dv != kEmpty && dv + dist_of(x) <= d;
             } else {
                 const uint32_t y = lv[j];
                 const uint32_t dh = map_find(p.htab + bk, mk - 1, hub_of(y));
-                hit = dh != kEmpty && dh + dist_of(y) <= p.d;
+                hit = dh != kEmpty && dh + dist_of(y) <= d;
             }
             ++probed;
             if (hit) atomicOr(pm_sm, 1u << k);
@@ -559,6 +564,8 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
     uint32_t* M = S + S_CAP;
     unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
     unsigned long long c_pref = 0;
+    if (p.ctr->done) return;
+    const uint32_t d = p.ctr->d;
     const int nlist = *p.list_n;
     for (int i = blockIdx.x * nwarps + wib; i < nlist; i += gridDim.x * nwarps) {
         __syncwarp();
@@ -611,8 +618,8 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3], c_probed,
-                                             tv, c_pref);
+            const unsigned okm = check_chunk(p, d, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3],
+                                             c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
@@ -654,7 +661,7 @@ enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_HI = 4, SH_TMP = 5, SH
 // them and appends the survivors to this block's global scratch, copied to
 // the new frontier at the end.  L(v) is staged into the shared-memory map when it fits;
 // otherwise membership in L(v) is a binary search in its row.
-__device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
+__device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
                                 uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst, int* hist, uint32_t* tv,
                                 unsigned long long* cnt) {
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -719,8 +726,8 @@ __device__ void gp_block_vertex(const GpParams& p, int32_t v, uint32_t* S, uint3
             bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
             if (!useM && valid && row_find(lv, ll, h) != kEmpty) valid = false;  // already a hub of v
-            const unsigned okm = check_chunk(p, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid], cnt[4],
-                                             tv, cnt[7]);
+            const unsigned okm = check_chunk(p, d, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid],
+                                             cnt[4], tv, cnt[7]);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
             base = __shfl_sync(kFull, base, 0);
@@ -763,9 +770,11 @@ __global__ void __launch_bounds__(512, 1) k_gp_block(GpParams p) {
     uint32_t* C = M + (1 << p.log_m);
     uint32_t* gacc = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
     unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (p.ctr->done) return;
+    const uint32_t d = p.ctr->d;
     const int n1 = *p.list_n;
     for (int i = blockIdx.x; i < n1; i += gridDim.x) {
-        gp_block_vertex(p, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, hist, tv, cnt);
+        gp_block_vertex(p, d, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, hist, tv, cnt);
         __syncthreads();
     }
     cnt[1] = warp_sum(cnt[1]);
@@ -787,7 +796,8 @@ __global__ void __launch_bounds__(512, 1) k_gp_block(GpParams p) {
 // ------------------------------------------------------------ probe index
 // Table size of row x: 2^ceil(log2(2|L(x)|)) for rows of >= kIndexMinLen
 // entries, else 0 (those rows are always scanned, never probed).
-__global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz) {
+__global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const RoundCounters* ctr) {
+    if (ctr->done) return;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = loff[x + 1] - loff[x];
         hsz[x] = l >= kIndexMinLen ? (int64_t(1) << ceil_log2_i64(2 * l)) : 0;
@@ -829,8 +839,10 @@ constexpr int kIndexWarps = 8;
 constexpr int kIndexSmemSlots = 2048;
 
 __global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t* loff, const uint32_t* lent,
-                                                                  const int64_t* hoff, uint32_t* htab, int64_t n) {
+                                                                  const int64_t* hoff, uint32_t* htab, int64_t n,
+                                                                  const RoundCounters* ctr) {
     extern __shared__ uint32_t ibuf[];
+    if (ctr->done) return;
     const int lane = lane_id(), w = threadIdx.x >> 5;
     uint32_t* buf = ibuf + w * kIndexSmemSlots;
     const int64_t nwarps = (int64_t)gridDim.x * kIndexWarps;
@@ -867,6 +879,7 @@ __global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t*
 // next active list + per-vertex new row lengths
 __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int64_t n, int64_t* newlen, int32_t* A,
                               RoundCounters* ctr) {
+    if (ctr->done) return;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = fcount(fse_new[v]);
         newlen[v] = (loff[v + 1] - loff[v]) + c;
@@ -897,6 +910,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_rows_warp(const uint64
                                                                    int32_t* big, int32_t* giant) {
     __shared__ uint32_t buf[kSortWarps][kWarpSortMax];
     const int lane = lane_id(), w = threadIdx.x >> 5;
+    if (ctr->done) return;
     const int nA = ctr->nA;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += nw) {
@@ -939,8 +953,10 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_rows_warp(const uint64
 
 __global__ void __launch_bounds__(1024) k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new,
                                                           const int32_t* big, const int* nbig,
-                                                          uint32_t* scratch, int64_t scratch_words) {
+                                                          uint32_t* scratch, int64_t scratch_words,
+                                                          const RoundCounters* ctr) {
     extern __shared__ uint32_t sbuf[];
+    if (ctr->done) return;
     const int nBig = *nbig;
     for (int i = blockIdx.x; i < nBig; i += gridDim.x) {
         const uint64_t f = fse_new[big[i]];
@@ -959,8 +975,9 @@ __global__ void __launch_bounds__(1024) k_sort_rows_block(const uint64_t* fse_ne
 
 // Old entries move to their place in the merged row: flat over old entries.
 __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
-                            const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n) {
+                            const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n, const RoundCounters* ctr) {
     __shared__ int64_t sh_r[2];
+    if (ctr->done) return;
     const int64_t total = loff[n];
     const int64_t ntiles = (total + kTileItems - 1) / kTileItems;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -984,7 +1001,9 @@ __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int
 // New entries (dist d) of each active vertex: warp per vertex.
 __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
                             const uint64_t* fse_new, const uint32_t* fhub_new, const int32_t* A,
-                            const RoundCounters* ctr, uint32_t d, uint32_t* top) {
+                            const RoundCounters* ctr, uint32_t* top) {
+    if (ctr->done) return;
+    const uint32_t d = ctr->d;
     const int nA = ctr->nA;
     const int lane = lane_id();
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -1013,6 +1032,76 @@ __global__ void k_top_init(uint32_t* top, int64_t n) {
         top[i] = 0u;
 }
 
+
+// ------------------------------------------------------------ loop control
+// Host-driven rounds: set the round number.
+__global__ void k_set_round(RoundCounters* ctr, uint32_t d) { ctr->d = d; }
+
+// Graph-driven rounds (one thread each).
+// Begin: next round number.
+__global__ void k_g_begin(RoundCounters* ctr) {
+    if (ctr->done) return;
+    ctr->d += 1;
+}
+
+// After the gather/prune kernels: stop on a capacity problem (resume on the
+// host), on an empty round (finished) or on a distance above 254; else
+// account the new labels and record the round's statistics.
+__global__ void k_g_check(RoundCounters* ctr, RoundStat* stats) {
+    if (ctr->done) return;
+    const unsigned d = ctr->d;
+    const long long acc = (long long)ctr->accepted;
+    if (ctr->fovf || ctr->guard) {
+        ctr->fallback = 1;
+        ctr->done = 1;
+        return;
+    }
+    if (d < PLB_MAX_ROUNDS) {
+        RoundStat& r = stats[d];
+        r.receivers = ctr->nR + ctr->nO1_base;
+        r.accepted = acc;
+        r.uniq = (long long)ctr->uniq;
+        r.probed = (long long)ctr->probed;
+        r.msgs = (long long)ctr->msgs;
+        r.pref = (long long)ctr->prefiltered;
+        r.arcs = (long long)ctr->arcs;
+        r.staged = (long long)ctr->staged;
+        r.tier0 = (long long)ctr->tier[0];
+        r.tier1 = (long long)ctr->tier[1];
+    }
+    if (acc == 0) {
+        ctr->done = 1;
+        return;
+    }
+    if (d > PLB_MAX_DIST) {
+        ctr->err = PLB_ERR_DIST_OVERFLOW;
+        ctr->done = 1;
+        return;
+    }
+    const long long T = ctr->T + acc;
+    if (T > ctr->lcap || 4 * T > ctr->hcap) {  // the merge or the probe index would not fit
+        ctr->fallback = 1;
+        ctr->done = 1;
+        return;
+    }
+    ctr->T = T;
+}
+
+// End of a completed round: flip the buffer parity, clear the per-round counters.
+__global__ void k_g_finish(RoundCounters* ctr) {
+    if (ctr->done) return;
+    ctr->cur ^= 1;
+    ctr->cursor = ctr->accepted = ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = 0;
+    ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;
+    ctr->bound_sum = ctr->prefiltered = 0;
+    ctr->nR = ctr->nO1 = ctr->nO2 = ctr->nBig = ctr->nGiant = 0;
+    ctr->nO1_base = ctr->nO2_base = ctr->fovf = 0;
+}
+
+// Loop condition of the graph: continue while not done.
+__global__ void k_g_cond(const RoundCounters* ctr, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, ctr->done ? 0u : 1u);
+}
 
 // ------------------------------------------------------------ finalize
 __global__ void k_final_len(const int64_t* loff, const int32_t* inv, int64_t n, int64_t* len) {

@@ -25,23 +25,28 @@ __global__ void k_after_collect(RoundCounters* ctr);
 __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n);
 __global__ void k_gp_warp(GpParams p);
 __global__ void k_gp_block(GpParams p);
-__global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz);
+__global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const RoundCounters* ctr);
 __global__ void k_index_clear(uint32_t* htab, const int64_t* hoff_n);
 __global__ void k_index_fill(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
                              int64_t n);
 __global__ void k_index_build(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
-                              int64_t n);
+                              int64_t n, const RoundCounters* ctr);
+__global__ void k_set_round(RoundCounters* ctr, uint32_t d);
+__global__ void k_g_begin(RoundCounters* ctr);
+__global__ void k_g_check(RoundCounters* ctr, RoundStat* stats);
+__global__ void k_g_finish(RoundCounters* ctr);
+__global__ void k_g_cond(const RoundCounters* ctr, cudaGraphConditionalHandle h);
 __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int64_t n, int64_t* newlen, int32_t* A,
                               RoundCounters* ctr);
 __global__ void k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* A, RoundCounters* ctr,
                                  int32_t* big, int32_t* giant);
 __global__ void k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* big, const int* nbig,
-                                  uint32_t* scratch, int64_t scratch_words);
+                                  uint32_t* scratch, int64_t scratch_words, const RoundCounters* ctr);
 __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
-                            const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n);
+                            const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n, const RoundCounters* ctr);
 __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
                             const uint64_t* fse_new, const uint32_t* fhub_new, const int32_t* A,
-                            const RoundCounters* ctr, uint32_t d, uint32_t* top);
+                            const RoundCounters* ctr, uint32_t* top);
 __global__ void k_top_init(uint32_t* top, int64_t n);
 __global__ void k_final_len(const int64_t* loff, const int32_t* inv, int64_t n, int64_t* len);
 __global__ void k_finalize(const int64_t* loff, const uint32_t* lent, const int32_t* inv, const int64_t* out_off,

@@ -246,3 +246,37 @@ def test_chunglu20_full_oracle(chunglu20):
     g, order, lab = chunglu20
     ref = O.pll(g.off, g.col, order)
     assert_labels_equal(lab, ref, "chunglu20")
+
+
+def test_graph_mode_bit_exact(rmat12):
+    """The round loop as one captured CUDA graph gives the same labels, the
+    same per-round counts, and handles the terminating round on the device."""
+    g, order, ref = rmat12
+    lab = gpu_build(g, order, use_graph=1)
+    assert_labels_equal(lab, ref, "graph mode")
+    host = gpu_build(g, order).stats()
+    st = lab.stats()
+    assert st["rounds"] == host["rounds"] and st["accepted"] == host["accepted"]
+    assert st["unique_round"] == host["unique_round"]
+    for gi in (G.small_graph(2), G.from_edges(40, [(0, i) for i in range(1, 40)])):
+        o = G.degree_order(gi)
+        assert_labels_equal(gpu_build(gi, o, use_graph=1), O.pll(gi.off, gi.col, o), "graph mode small")
+
+
+def test_graph_mode_capacity_fallback():
+    """K_1500 accepts 1.1M labels in round 1, more than the graph-mode label
+    capacity (2^20): the round is redone host-driven, labels unchanged."""
+    n = 1500
+    g = G.from_edges(n, [(i, j) for i in range(n) for j in range(i + 1, n)])
+    order = np.arange(n, dtype=np.int32)
+    lab = gpu_build(g, order, use_graph=1)
+    assert lab.total == n * (n + 1) // 2
+    assert lab.stats()["reruns"] >= 1
+    assert_labels_equal(lab, O.pll(g.off, g.col, order), "K1500")
+
+
+def test_graph_mode_distance_overflow():
+    g = G.from_edges(300, [(i, i + 1) for i in range(299)])
+    with pytest.raises(plb.PLBError) as e:
+        gpu_build(g, np.arange(300, dtype=np.int32), use_graph=1)
+    assert e.value.code == plb.PLB_ERR_DIST_OVERFLOW
