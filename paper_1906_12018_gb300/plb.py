@@ -321,8 +321,10 @@ def build_batch(graphs: Sequence, options: Options | None = None, stream=None, *
         _dev(o, torch.int32, "order")
         orders[i] = o.data_ptr() if o.numel() else None
     outs = (ctypes.c_void_p * max(k, 1))()
-    opt = options if options is not None else default_options(**kw)
-    _check(_lib().plb_build_batch(csrs, orders, k, ctypes.byref(opt), _stream(stream), outs), "plb_build_batch")
+    # no options: the library's batch defaults (round loop as a captured CUDA graph)
+    opt = options if options is not None else (default_options(**kw) if kw else None)
+    _check(_lib().plb_build_batch(csrs, orders, k, ctypes.byref(opt) if opt is not None else None,
+                                  _stream(stream), outs), "plb_build_batch")
     return [Labels(outs[i]) for i in range(k)]
 
 
