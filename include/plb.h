@@ -212,6 +212,11 @@ int plb_degree_order_noalloc(const plb_csr* g, int32_t* order_out, plb_stream st
 /* Human-readable status text (static storage). */
 const char* plb_strerror(int status);
 
+/* Where the last PLB_ERR_CUDA of a build on this host thread came from: the
+ * library call site and CUDA's error name and text (static, thread-local
+ * storage; "" if none). */
+const char* plb_last_error(void);
+
 /* ABI version: 100 * major + minor. */
 int plb_version(void);
 

@@ -9,6 +9,7 @@ namespace plb {
 
 int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
                const plb_options& o, cudaStream_t s, plb_labels** out);
+extern thread_local char g_last_error[256];
 
 namespace {
 
@@ -352,5 +353,7 @@ const char* plb_strerror(int status) {
 }
 
 int plb_version(void) { return 100; }
+
+const char* plb_last_error(void) { return plb::g_last_error; }
 
 }  // extern "C"

@@ -2,6 +2,7 @@
 // round loop of Alg. 3 (Sec. 3.1) and the final by-id label layout.
 #include <algorithm>
 #include <cstddef>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -91,6 +92,17 @@ int num_sms() {
     return sms;
 }
 
+}  // namespace
+
+thread_local char g_last_error[256] = "";
+
+void set_last_error(cudaError_t e, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "plb_build.cu:%d: %s (%s)", line, cudaGetErrorString(e),
+             cudaGetErrorName(e));
+}
+
+namespace {
+
 int pow2_at_least(int64_t x) {
     int p = 1;
     while (p < x) p <<= 1;
@@ -103,12 +115,14 @@ int pow2_at_least(int64_t x) {
 // *out holds the labels (rows by original id).
 int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
                const plb_options& o, cudaStream_t s, plb_labels** out) {
-#define PLB_CK(x)                                   \
-    do {                                            \
-        if ((x) != cudaSuccess) {                   \
-            (void)cudaGetLastError();               \
-            return PLB_ERR_CUDA;                    \
-        }                                           \
+#define PLB_CK(x)                                            \
+    do {                                                     \
+        const cudaError_t plb_e_ = (x);                      \
+        if (plb_e_ != cudaSuccess) {                         \
+            (void)cudaGetLastError();                        \
+            set_last_error(plb_e_, __LINE__);                \
+            return PLB_ERR_CUDA;                             \
+        }                                                    \
     } while (0)
 #define PLB_ALLOC_OK() \
     do {               \
@@ -404,6 +418,15 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         cudaGraphNode_t cnode;
         PLB_CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
         cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // capture on a private stream (capture is not allowed on the legacy
+        // default stream); the graph itself is launched on the caller's stream
+        cudaStream_t user_stream = s, cap_stream = nullptr;
+        PLB_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+        struct StreamGuard {
+            cudaStream_t st;
+            ~StreamGuard() { cudaStreamDestroy(st); }
+        } sguard{cap_stream};
+        s = cap_stream;
         PLB_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = cudaSuccess;
         const int64_t launches0 = st.launches;
@@ -429,8 +452,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
         k_g_cond<<<1, 1, 0, s>>>(ctr, handle);
         const cudaError_t ee = cudaStreamEndCapture(s, &body);
+        s = user_stream;
         if (ce != cudaSuccess || ee != cudaSuccess) {
             (void)cudaGetLastError();
+            set_last_error(ce != cudaSuccess ? ce : ee, __LINE__);
             return PLB_ERR_CUDA;
         }
         const int64_t per_pair = st.launches - launches0 + 1;

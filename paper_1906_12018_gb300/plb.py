@@ -32,6 +32,10 @@ class PLBError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
         msg = _lib().plb_strerror(code).decode() if _LIB is not None else f"status {code}"
+        if code == PLB_ERR_CUDA and _LIB is not None:
+            detail = _lib().plb_last_error().decode()
+            if detail:
+                msg += f" [{detail}]"
         super().__init__(f"{what}: {msg} (status {code})" if what else msg)
 
 
@@ -173,6 +177,8 @@ def _lib():
     lib.plb_degree_order_noalloc.restype = I
     lib.plb_strerror.argtypes = [I]
     lib.plb_strerror.restype = ctypes.c_char_p
+    lib.plb_last_error.argtypes = []
+    lib.plb_last_error.restype = ctypes.c_char_p
     lib.plb_version.argtypes = []
     lib.plb_version.restype = I
     _LIB = lib
@@ -184,7 +190,7 @@ def exported_symbols() -> list[str]:
     return ["plb_default_options", "plb_build", "plb_build_batch", "plb_query_batch", "plb_query_multi",
             "plb_labels_view", "plb_labels_stats", "plb_labels_bytes", "plb_labels_free", "plb_release_cached_memory",
             "plb_degree_order",
-            "plb_degree_order_noalloc", "plb_strerror", "plb_version"]
+            "plb_degree_order_noalloc", "plb_strerror", "plb_last_error", "plb_version"]
 
 
 def _check(code: int, what: str):
