@@ -307,9 +307,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.gscratch_words = std::max<int64_t>(n, 1);
         return p;
     };
+    const int* skip = nullptr;  // graph mode: &ctr->done (scans of finished rounds do nothing)
     auto launch_frontier = [&](int c, int x) -> cudaError_t {
         k_active_degree<<<gflat, kFlatThreads, 0, s>>>(roff, A, ctr, tmp64, n);
-        cudaError_t e = exclusive_scan_i64(tmp64, aoff, n, scan_scr, s);
+        cudaError_t e = exclusive_scan_i64(tmp64, aoff, n, scan_scr, s, skip);
         if (e != cudaSuccess) return e;
         k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[c], fhub[c], A, aoff, ctr, recv, n);
         k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[c], n, fse[x], R, O1, ctr, lim);
@@ -346,7 +347,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                                                                         0, ctr);
         k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[x], fhub[x], giant, &ctr->nGiant,
                                                                             sortscr, sort_words, ctr);
-        cudaError_t e = exclusive_scan_i64(tmp64, loff[x], n, scan_scr, s);
+        cudaError_t e = exclusive_scan_i64(tmp64, loff[x], n, scan_scr, s, skip);
         if (e != cudaSuccess) return e;
         k_merge_old<<<flat_grid_cap, kFlatThreads, 0, s>>>(loff[c], lent[c], loff[x], lent[x], fse[x], fhub[x], n,
                                                            ctr);
@@ -427,6 +428,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             ~StreamGuard() { cudaStreamDestroy(st); }
         } sguard{cap_stream};
         s = cap_stream;
+        skip = &ctr->done;
         PLB_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = cudaSuccess;
         const int64_t launches0 = st.launches;
@@ -441,7 +443,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             }
             if (ce == cudaSuccess) {
                 k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[x], n, tmp64, ctr);
-                ce = exclusive_scan_i64(tmp64, hoff, n, scan_scr, s);
+                ce = exclusive_scan_i64(tmp64, hoff, n, scan_scr, s, skip);
             }
             if (ce == cudaSuccess) {
                 k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t), s>>>(
@@ -453,6 +455,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         k_g_cond<<<1, 1, 0, s>>>(ctr, handle);
         const cudaError_t ee = cudaStreamEndCapture(s, &body);
         s = user_stream;
+        skip = nullptr;
         if (ce != cudaSuccess || ee != cudaSuccess) {
             (void)cudaGetLastError();
             set_last_error(ce != cudaSuccess ? ce : ee, __LINE__);

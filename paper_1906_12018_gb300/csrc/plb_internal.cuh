@@ -35,34 +35,38 @@ __device__ __forceinline__ uint32_t hslot(uint32_t key, int logcap) {
 // Insert key into an open-addressing set; returns true if it was new.
 // The caller guarantees the table never fills (load <= 1/2 plus the number
 // of concurrently inserting threads).
+// (Every probe loop below is bounded by the table size, so a table broken by
+// a bug can never spin a kernel forever.)
 __device__ __forceinline__ bool set_insert(uint32_t* tab, int logcap, uint32_t key) {
     const uint32_t mask = (1u << logcap) - 1u;
     uint32_t s = hslot(key, logcap);
-    while (true) {
+    for (uint32_t i = 0; i <= mask; ++i) {
         const uint32_t old = atomicCAS(tab + s, kEmpty, key);
         if (old == kEmpty) return true;
         if (old == key) return false;
         s = (s + 1) & mask;
     }
+    return false;
 }
 
 // Insert a packed label entry keyed by its hub (keys unique by construction).
 __device__ __forceinline__ void map_insert(uint32_t* tab, int logcap, uint32_t e) {
     const uint32_t mask = (1u << logcap) - 1u;
     uint32_t s = hslot(hub_of(e), logcap);
-    while (atomicCAS(tab + s, kEmpty, e) != kEmpty) s = (s + 1) & mask;
+    for (uint32_t i = 0; i <= mask && atomicCAS(tab + s, kEmpty, e) != kEmpty; ++i) s = (s + 1) & mask;
 }
 
 // Distance stored for hub w, or 0xFFFFFFFF when w is not in the map.
 __device__ __forceinline__ uint32_t map_find(const uint32_t* tab, int logcap, uint32_t w) {
     const uint32_t mask = (1u << logcap) - 1u;
     uint32_t s = hslot(w, logcap);
-    while (true) {
+    for (uint32_t i = 0; i <= mask; ++i) {
         const uint32_t x = tab[s];
         if (x == kEmpty) return kEmpty;
         if (hub_of(x) == w) return dist_of(x);
         s = (s + 1) & mask;
     }
+    return kEmpty;
 }
 
 __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
@@ -167,7 +171,7 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 // Device-wide exclusive scan of int64 values; out may alias in.
 // count(i) is evaluated for i in [0, n) and out[n] receives the total.
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* block_sums,
-                               cudaStream_t s);
+                               cudaStream_t s, const int* skip = nullptr);
 int64_t scan_scratch_elems(int64_t n);
 
 }  // namespace plb

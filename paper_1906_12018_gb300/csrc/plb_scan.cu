@@ -43,8 +43,9 @@ __device__ int64_t block_excl_scan(int64_t x, int64_t* sh_warp, int64_t* total) 
 }
 
 __global__ void __launch_bounds__(kThreads) k_scan_tiles(const int64_t* in, int64_t* out, int64_t n,
-                                                         int64_t* tile_sums) {
+                                                         int64_t* tile_sums, const int* skip) {
     __shared__ int64_t sh_warp[kThreads / 32 + 1];
+    if (skip && *skip) return;
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kPerThread;
     int64_t v[kPerThread];
     int64_t sum = 0;
@@ -65,7 +66,9 @@ __global__ void __launch_bounds__(kThreads) k_scan_tiles(const int64_t* in, int6
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kThreads) k_scan_add(int64_t* out, int64_t n, const int64_t* tile_offs) {
+__global__ void __launch_bounds__(kThreads) k_scan_add(int64_t* out, int64_t n, const int64_t* tile_offs,
+                                                       const int* skip) {
+    if (skip && *skip) return;
     const int64_t add = tile_offs[blockIdx.x];
     const int64_t base = (int64_t)blockIdx.x * kTile;
     for (int k = threadIdx.x; k < kTile; k += kThreads) {
@@ -75,8 +78,10 @@ __global__ void __launch_bounds__(kThreads) k_scan_add(int64_t* out, int64_t n, 
 }
 
 // single-tile scan writing out[n] = total
-__global__ void __launch_bounds__(kThreads) k_scan_single(const int64_t* in, int64_t* out, int64_t n) {
+__global__ void __launch_bounds__(kThreads) k_scan_single(const int64_t* in, int64_t* out, int64_t n,
+                                                          const int* skip) {
     __shared__ int64_t sh_warp[kThreads / 32 + 1];
+    if (skip && *skip) return;
     const int64_t base = (int64_t)threadIdx.x * kPerThread;
     int64_t v[kPerThread];
     int64_t sum = 0;
@@ -97,6 +102,11 @@ __global__ void __launch_bounds__(kThreads) k_scan_single(const int64_t* in, int
     if (threadIdx.x == 0) out[n] = total;
 }
 
+__global__ void k_scan_total(int64_t* dst, const int64_t* src, const int* skip) {
+    if (skip && *skip) return;
+    *dst = *src;
+}
+
 }  // namespace
 
 int64_t scan_scratch_elems(int64_t n) {
@@ -109,21 +119,22 @@ int64_t scan_scratch_elems(int64_t n) {
     return total + 1;
 }
 
-// out[0..n] = exclusive scan of in[0..n), out[n] = sum.
-cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* scratch, cudaStream_t s) {
+// out[0..n] = exclusive scan of in[0..n), out[n] = sum.  With skip, every
+// kernel returns at once while *skip is non-zero (graph-driven rounds after
+// the loop has finished).
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* scratch, cudaStream_t s,
+                               const int* skip) {
     if (n <= kTile) {
-        k_scan_single<<<1, kThreads, 0, s>>>(in, out, n);
+        k_scan_single<<<1, kThreads, 0, s>>>(in, out, n, skip);
         return cudaGetLastError();
     }
     const int64_t tiles = (n + kTile - 1) / kTile;
     int64_t* sums = scratch;  // tiles + 1 entries
-    k_scan_tiles<<<(unsigned)tiles, kThreads, 0, s>>>(in, out, n, sums);
-    cudaError_t e = exclusive_scan_i64(sums, sums, tiles, scratch + tiles + 1, s);
+    k_scan_tiles<<<(unsigned)tiles, kThreads, 0, s>>>(in, out, n, sums, skip);
+    cudaError_t e = exclusive_scan_i64(sums, sums, tiles, scratch + tiles + 1, s, skip);
     if (e != cudaSuccess) return e;
-    k_scan_add<<<(unsigned)tiles, kThreads, 0, s>>>(out, n, sums);
-    // total = sums[tiles]
-    e = cudaMemcpyAsync(out + n, sums + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)tiles, kThreads, 0, s>>>(out, n, sums, skip);
+    k_scan_total<<<1, 1, 0, s>>>(out + n, sums + tiles, skip);  // total = sums[tiles]
     return cudaGetLastError();
 }
 
