@@ -194,7 +194,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                                                                                           roff, rcol, n, nnz);
         PLB_CK(cudaGetLastError());
     }
-    st.launches += 4;
+    st.launches += 3 + scan_launch_count(n);
+    const int scan_n = scan_launch_count(n);  // launches of one scan over n values
 
     // ------------------------------------------------------------ state
     int64_t lcap[2] = {std::max<int64_t>(2 * n, 1024), std::max<int64_t>(2 * n, 1024)};
@@ -219,6 +220,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     uint32_t* top = pool.alloc<uint32_t>(n * kTopRow);
     PLB_ALLOC_OK();
     k_top_init<<<flat_grid_cap, kFlatThreads, 0, s>>>(top, n);
+    st.launches += 1;
     // probe index of L (hub-keyed table per long row), rebuilt after each merge
     int64_t* hoff = pool.alloc<int64_t>(n + 1);
     int64_t hcap = std::max<int64_t>(4 * n, 1024);
@@ -237,7 +239,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
         k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t), s>>>(
             loff[which], lent[which], hoff, htab, n, ctr);
-        st.launches += 4;
+        st.launches += 2 + scan_n;
         return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
     };
     {
@@ -315,7 +317,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[c], fhub[c], A, aoff, ctr, recv, n);
         k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[c], n, fse[x], R, O1, ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(ctr);
-        st.launches += 7;
+        st.launches += 4 + scan_n;
         return cudaGetLastError();
     };
     auto launch_gp = [&](GpParams p, cudaEvent_t* g1) -> cudaError_t {
@@ -353,7 +355,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                                                            ctr);
         k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
             loff[c], lent[c], loff[x], lent[x], fse[x], fhub[x], A, ctr, top);
-        st.launches += 9;
+        st.launches += 6 + scan_n;
         return cudaGetLastError();
     };
 
@@ -361,162 +363,20 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int d = 0;          // last completed round
     bool finished = false;
     std::vector<std::pair<int, cudaEvent_t>> round_ev;  // (round, start event)
+    std::vector<char> host_stat(PLB_MAX_ROUNDS, 0);     // rounds whose statistics the host recorded
 
-    // ---- graph mode: the whole round loop as one CUDA graph with a device-side
-    // while condition (two rounds per body: the buffer parities alternate)
-    if (o.use_graph) {
-        const int64_t lc = std::max<int64_t>(std::max<int64_t>(32 * n, T + 1024), 1 << 20);
-        auto grow = [&](uint32_t*& buf, int64_t& cap, int64_t want, int64_t keep) -> bool {
-            if (cap >= want) return true;
-            uint32_t* nb = pool.alloc<uint32_t>(want);
-            if (pool.failed) return false;
-            if (keep > 0 && cudaMemcpyAsync(nb, buf, sizeof(uint32_t) * keep, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return false;
-            pool.release(buf);
-            buf = nb;
-            cap = want;
-            return true;
-        };
-        for (int b = 0; b < 2; ++b) {
-            if (!grow(lent[b], lcap[b], lc, b == cur ? T : 0) || !grow(fhub[b], fcap[b], lc, b == cur ? n : 0))
-                return PLB_ERR_OOM;
-        }
-        if (!grow(htab, hcap, 4 * lc, 0)) return PLB_ERR_OOM;
-        {
-            const int e = build_index(cur, T);  // the index of the current labels in the grown table
-            if (e != PLB_OK) return e;
-        }
-        RoundStat* dstat = pool.alloc<RoundStat>(PLB_MAX_ROUNDS);
-        PLB_ALLOC_OK();
-        PLB_CK(cudaMemsetAsync(dstat, 0, sizeof(RoundStat) * PLB_MAX_ROUNDS, s));
-        PLB_CK(cudaStreamSynchronize(s));
-        hctr->T = T;
-        hctr->lcap = lc;
-        hctr->fcap = lc;
-        hctr->hcap = 4 * lc;
-        hctr->cur = cur;
-        PLB_CK(cudaMemcpyAsync(&ctr->cur, &hctr->cur, sizeof(int), cudaMemcpyHostToDevice, s));
-        PLB_CK(cudaMemcpyAsync(&ctr->T, &hctr->T, 4 * sizeof(long long), cudaMemcpyHostToDevice, s));
-        cudaEvent_t ga = tm.on ? tm.mark() : nullptr;
-        cudaGraph_t graph = nullptr;
-        cudaGraphExec_t exec = nullptr;
-        struct GraphGuard {
-            cudaGraph_t* g;
-            cudaGraphExec_t* e;
-            ~GraphGuard() {
-                if (*e) cudaGraphExecDestroy(*e);
-                if (*g) cudaGraphDestroy(*g);
-            }
-        } gguard{&graph, &exec};
-        PLB_CK(cudaGraphCreate(&graph, 0));
-        cudaGraphConditionalHandle handle;
-        PLB_CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-        cudaGraphNodeParams cp = {};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = handle;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        cudaGraphNode_t cnode;
-        PLB_CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        // capture on a private stream (capture is not allowed on the legacy
-        // default stream); the graph itself is launched on the caller's stream
-        cudaStream_t user_stream = s, cap_stream = nullptr;
-        PLB_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
-        struct StreamGuard {
-            cudaStream_t st;
-            ~StreamGuard() { cudaStreamDestroy(st); }
-        } sguard{cap_stream};
-        s = cap_stream;
-        skip = &ctr->done;
-        PLB_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = cudaSuccess;
-        const int64_t launches0 = st.launches;
-        for (int r = 0; r < 2 && ce == cudaSuccess; ++r) {
-            const int c = cur ^ r, x = c ^ 1;
-            k_g_begin<<<1, 1, 0, s>>>(ctr);
-            ce = launch_frontier(c, x);
-            if (ce == cudaSuccess) ce = launch_gp(gp_params(c, x, lc), nullptr);
-            if (ce == cudaSuccess) {
-                k_g_check<<<1, 1, 0, s>>>(ctr, dstat);
-                ce = launch_merge(c, x);
-            }
-            if (ce == cudaSuccess) {
-                k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[x], n, tmp64, ctr);
-                ce = exclusive_scan_i64(tmp64, hoff, n, scan_scr, s, skip);
-            }
-            if (ce == cudaSuccess) {
-                k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t), s>>>(
-                    loff[x], lent[x], hoff, htab, n, ctr);
-                k_g_finish<<<1, 1, 0, s>>>(ctr);
-                ce = cudaGetLastError();
-            }
-        }
-        k_g_cond<<<1, 1, 0, s>>>(ctr, handle);
-        const cudaError_t ee = cudaStreamEndCapture(s, &body);
-        s = user_stream;
-        skip = nullptr;
-        if (ce != cudaSuccess || ee != cudaSuccess) {
-            (void)cudaGetLastError();
-            set_last_error(ce != cudaSuccess ? ce : ee, __LINE__);
-            return PLB_ERR_CUDA;
-        }
-        const int64_t per_pair = st.launches - launches0 + 1;
-        st.launches = launches0;
-        PLB_CK(cudaGraphInstantiate(&exec, graph, 0));
-        PLB_CK(cudaGraphLaunch(exec, s));
-        PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
-        std::vector<RoundStat> hstat(PLB_MAX_ROUNDS);
-        PLB_CK(cudaMemcpyAsync(hstat.data(), dstat, sizeof(RoundStat) * PLB_MAX_ROUNDS, cudaMemcpyDeviceToHost, s));
-        PLB_CK(cudaStreamSynchronize(s));
-        if (tm.on) tm.span(T_GPW, ga, tm.mark());
-        if (hctr->guard) return PLB_ERR_CUDA;
-        const int dd = (int)hctr->d;  // last round started
-        st.launches += per_pair * ((dd + 1) / 2);
-        for (int r = 1; r <= dd && r < PLB_MAX_ROUNDS; ++r) {
-            const RoundStat& x = hstat[r];
-            st.receivers[r] = x.receivers;
-            st.accepted[r] = x.accepted;
-            st.unique_round[r] = x.uniq;
-            st.prefiltered_round[r] = x.pref;
-            st.probed_round[r] = x.probed;
-            st.messages_round[r] = x.msgs;
-            st.arcs_scanned += x.arcs;
-            st.messages += x.msgs;
-            st.unique_candidates += x.uniq;
-            st.staged_entries += x.staged;
-            st.probed_entries += x.probed;
-            st.tier_vertices[0] += x.tier0;
-            st.tier_vertices[1] += x.tier1;
-        }
-        T = hctr->T;
-        cur = hctr->cur;
-        if (hctr->err) return hctr->err;
-        if (!hctr->fallback) {
-            d = dd;
-            finished = true;
-        } else {
-            // a capacity was exceeded in round dd: redo it on the host
-            d = dd - 1;
-            st.receivers[dd] = st.accepted[dd] = st.unique_round[dd] = 0;
-            hctr->nA = hctr->nA_saved;
-            PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
-            PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
-            PLB_CK(cudaMemcpyAsync(&ctr->nA, &hctr->nA, sizeof(int), cudaMemcpyHostToDevice, s));
-            PLB_CK(cudaMemsetAsync(&ctr->done, 0, sizeof(int) * 2, s));
-            st.reruns += 1;
-            // the index in htab is that of L[cur] (the round stopped before the merge)
-        }
-    }
-
-    // ---- host-driven rounds (from round d + 1)
-    while (!finished) {
+    // One host-driven round (d + 1).  With frontier_done the round's frontier
+    // step has already run (a graph stopped after it) and ctr->d holds d + 1.
+    auto host_round = [&](bool frontier_done) -> int {
         ++d;
         const int nxt = cur ^ 1;
         cudaEvent_t r0 = tm.on ? tm.mark() : nullptr;
-        k_set_round<<<1, 1, 0, s>>>(ctr, (uint32_t)d);
-        // frontier: mark receivers from the active list, collect them
-        PLB_CK(launch_frontier(cur, nxt));
+        if (!frontier_done) {
+            k_set_round<<<1, 1, 0, s>>>(ctr, (uint32_t)d);
+            st.launches += 1;
+            // frontier: mark receivers from the active list, collect them
+            PLB_CK(launch_frontier(cur, nxt));
+        }
         // size the new frontier buffer from the candidate bound (no re-run)
         PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
         PLB_CK(cudaStreamSynchronize(s));
@@ -566,6 +426,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             st.prefiltered_round[d] = (int64_t)hctr->prefiltered;
             st.probed_round[d] = (int64_t)hctr->probed;
             st.messages_round[d] = (int64_t)hctr->msgs;
+            host_stat[d] = 1;
             if (tm.on) round_ev.push_back({d, r0});
         }
         st.arcs_scanned += (int64_t)hctr->arcs;
@@ -574,10 +435,14 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         st.staged_entries += (int64_t)hctr->staged;
         st.probed_entries += (int64_t)hctr->probed;
         for (int k = 0; k < 3; ++k) st.tier_vertices[k] += (int64_t)hctr->tier[k];
-        if (acc == 0) break;
+        if (acc == 0) {
+            finished = true;
+            return PLB_OK;
+        }
         if (d > PLB_MAX_DIST) {
             status = PLB_ERR_DIST_OVERFLOW;
-            break;
+            finished = true;
+            return PLB_OK;
         }
         // merge: L <- L U dL_d (rows stay sorted by hub rank)
         cudaEvent_t m0 = tm.on ? tm.mark() : nullptr;
@@ -607,6 +472,211 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             fhub[nx2] = pool.alloc<uint32_t>(fcap[nx2]);
             PLB_ALLOC_OK();
         }
+        return PLB_OK;
+    };
+
+    // ---- graph mode: the round loop as one CUDA graph with a device-side while
+    // condition (two rounds per body: the buffer parities alternate).  The graph
+    // stops at a round that may not fit its buffers: before the gather when the
+    // round's candidate bound exceeds the new-frontier buffer (the round then
+    // continues host-driven), after it when its labels exceed the label buffers
+    // (they grow and the round's merge runs here).  The graph is then captured
+    // again and resumes with the next round.
+    if (o.use_graph) {
+        RoundStat* dstat = pool.alloc<RoundStat>(PLB_MAX_ROUNDS);
+        PLB_ALLOC_OK();
+        PLB_CK(cudaMemsetAsync(dstat, 0, sizeof(RoundStat) * PLB_MAX_ROUNDS, s));
+        int64_t lc = std::max<int64_t>(std::max<int64_t>(32 * n, T + 1024), 1 << 20);
+        auto grow = [&](uint32_t*& buf, int64_t& cap, int64_t want, int64_t keep) -> bool {
+            if (cap >= want) return true;
+            uint32_t* nb = pool.alloc<uint32_t>(want);
+            if (pool.failed) return false;
+            if (keep > 0 && cudaMemcpyAsync(nb, buf, sizeof(uint32_t) * keep, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return false;
+            pool.release(buf);
+            buf = nb;
+            cap = want;
+            return true;
+        };
+        for (int attempt = 0; attempt < 8 && !finished; ++attempt) {
+            if (!grow(lent[cur], lcap[cur], lc, T) || !grow(lent[cur ^ 1], lcap[cur ^ 1], lc, 0)) return PLB_ERR_OOM;
+            if (4 * std::min(lcap[0], lcap[1]) > hcap) {
+                pool.release(htab);
+                hcap = 4 * std::min(lcap[0], lcap[1]);
+                htab = pool.alloc<uint32_t>(hcap);
+                PLB_ALLOC_OK();
+                const int e = build_index(cur, T);  // the current labels' index in the new table
+                if (e != PLB_OK) return e;
+            }
+            PLB_CK(cudaStreamSynchronize(s));
+            hctr->d = (unsigned)d;
+            hctr->cur = cur;
+            hctr->T = T;
+            hctr->lcap = std::min(lcap[0], lcap[1]);
+            hctr->hcap = hcap;
+            hctr->fcap[0] = fcap[0];
+            hctr->fcap[1] = fcap[1];
+            PLB_CK(cudaMemcpyAsync(&ctr->d, &hctr->d, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+            PLB_CK(cudaMemcpyAsync(&ctr->cur, &hctr->cur, sizeof(int), cudaMemcpyHostToDevice, s));
+            PLB_CK(cudaMemcpyAsync(&ctr->T, &hctr->T, 5 * sizeof(long long), cudaMemcpyHostToDevice, s));
+            cudaEvent_t ga = tm.on ? tm.mark() : nullptr;
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            struct GraphGuard {
+                cudaGraph_t* g;
+                cudaGraphExec_t* e;
+                ~GraphGuard() {
+                    if (*e) cudaGraphExecDestroy(*e);
+                    if (*g) cudaGraphDestroy(*g);
+                }
+            } gguard{&graph, &exec};
+            PLB_CK(cudaGraphCreate(&graph, 0));
+            cudaGraphConditionalHandle handle;
+            PLB_CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            PLB_CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            // capture on a private stream (capture is not allowed on the legacy
+            // default stream); the graph itself is launched on the caller's stream
+            cudaStream_t user_stream = s, cap_stream = nullptr;
+            PLB_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+            struct StreamGuard {
+                cudaStream_t st;
+                ~StreamGuard() { cudaStreamDestroy(st); }
+            } sguard{cap_stream};
+            s = cap_stream;
+            skip = &ctr->done;
+            PLB_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            cudaError_t ce = cudaSuccess;
+            const int64_t launches0 = st.launches;
+            for (int r = 0; r < 2 && ce == cudaSuccess; ++r) {
+                const int c = cur ^ r, x = c ^ 1;
+                k_g_begin<<<1, 1, 0, s>>>(ctr);
+                ce = launch_frontier(c, x);
+                if (ce == cudaSuccess) {
+                    k_g_bound<<<1, 1, 0, s>>>(ctr, x);
+                    ce = launch_gp(gp_params(c, x, fcap[x]), nullptr);
+                }
+                if (ce == cudaSuccess) {
+                    k_g_check<<<1, 1, 0, s>>>(ctr, dstat);
+                    ce = launch_merge(c, x);
+                }
+                if (ce == cudaSuccess) {
+                    k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[x], n, tmp64, ctr);
+                    ce = exclusive_scan_i64(tmp64, hoff, n, scan_scr, s, skip);
+                }
+                if (ce == cudaSuccess) {
+                    k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t),
+                                    s>>>(loff[x], lent[x], hoff, htab, n, ctr);
+                    k_g_finish<<<1, 1, 0, s>>>(ctr);
+                    st.launches += 6 + scan_n;  // loop control (4) and the index rebuild
+                    ce = cudaGetLastError();
+                }
+            }
+            k_g_cond<<<1, 1, 0, s>>>(ctr, handle);
+            const cudaError_t ee = cudaStreamEndCapture(s, &body);
+            s = user_stream;
+            skip = nullptr;
+            if (ce != cudaSuccess || ee != cudaSuccess) {
+                (void)cudaGetLastError();
+                set_last_error(ce != cudaSuccess ? ce : ee, __LINE__);
+                return PLB_ERR_CUDA;
+            }
+            const int64_t per_pair = st.launches - launches0 + 1;
+            st.launches = launches0;
+            PLB_CK(cudaGraphInstantiate(&exec, graph, 0));
+            PLB_CK(cudaGraphLaunch(exec, s));
+            PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+            PLB_CK(cudaStreamSynchronize(s));
+            if (tm.on) tm.span(T_GPW, ga, tm.mark());
+            if (hctr->guard) return PLB_ERR_CUDA;
+            const int dd = (int)hctr->d;  // last round started
+            st.launches += per_pair * ((dd - d + 1) / 2);
+            T = hctr->T;
+            cur = hctr->cur;
+            if (hctr->err) {
+                d = dd;
+                status = hctr->err;
+                finished = true;
+                break;
+            }
+            if (!hctr->fallback) {
+                d = dd;
+                finished = true;
+                break;
+            }
+            st.reruns += 1;
+            PLB_CK(cudaMemsetAsync(&ctr->done, 0, sizeof(int) * 2, s));
+            if (hctr->fallback == kStopBeforeGather) {
+                // round dd's candidate bound exceeds the new-frontier buffer:
+                // the round continues host-driven from its gather
+                d = dd - 1;
+                const int e = host_round(true);
+                if (e != PLB_OK) return e;
+                continue;
+            }
+            if (hctr->fovf) {
+                // the new frontier of round dd overflowed its buffer: restore the
+                // round's start state and redo it host-driven
+                d = dd - 1;
+                hctr->nA = hctr->nA_saved;
+                PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
+                PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
+                PLB_CK(cudaMemcpyAsync(&ctr->nA, &hctr->nA, sizeof(int), cudaMemcpyHostToDevice, s));
+                const int e = host_round(false);
+                if (e != PLB_OK) return e;
+                continue;
+            }
+            // the labels of round dd do not fit the label buffers: its gather is
+            // complete, so grow the merge target and finish the round here
+            const int nxt = cur ^ 1;
+            const int64_t Tn = T + (int64_t)hctr->accepted;
+            lc = std::max<int64_t>(Tn + Tn / 2, lc + lc / 2);
+            if (!grow(lent[nxt], lcap[nxt], lc, 0)) return PLB_ERR_OOM;
+            PLB_CK(launch_merge(cur, nxt));
+            T = Tn;
+            cur = nxt;
+            d = dd;
+            {
+                const int e = build_index(cur, T);
+                if (e != PLB_OK) return e;
+            }
+            PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
+            PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
+        }
+        // per-round statistics written on the device
+        std::vector<RoundStat> hstat(PLB_MAX_ROUNDS);
+        PLB_CK(cudaMemcpyAsync(hstat.data(), dstat, sizeof(RoundStat) * PLB_MAX_ROUNDS, cudaMemcpyDeviceToHost, s));
+        PLB_CK(cudaStreamSynchronize(s));
+        for (int r = 1; r <= d && r < PLB_MAX_ROUNDS; ++r) {
+            if (host_stat[r]) continue;
+            const RoundStat& x = hstat[r];
+            st.receivers[r] = x.receivers;
+            st.accepted[r] = x.accepted;
+            st.unique_round[r] = x.uniq;
+            st.prefiltered_round[r] = x.pref;
+            st.probed_round[r] = x.probed;
+            st.messages_round[r] = x.msgs;
+            st.arcs_scanned += x.arcs;
+            st.messages += x.msgs;
+            st.unique_candidates += x.uniq;
+            st.staged_entries += x.staged;
+            st.probed_entries += x.probed;
+            st.tier_vertices[0] += x.tier0;
+            st.tier_vertices[1] += x.tier1;
+        }
+        // (after 8 graph segments the remaining rounds run host-driven)
+    }
+
+    // ---- host-driven rounds (from round d + 1)
+    while (!finished) {
+        const int e = host_round(false);
+        if (e != PLB_OK) return e;
     }
     st.rounds = d;
     st.total_labels = T;
@@ -644,7 +714,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         return fail(PLB_ERR_CUDA);
     if (cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return fail(PLB_ERR_CUDA);
-    st.launches += 4;
+    st.launches += 2 + scan_n;
     cudaEvent_t f1 = tm.on ? tm.mark() : nullptr;
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(PLB_ERR_CUDA);
     L->max_dist = (int32_t)hctr->max_dist;

@@ -173,5 +173,6 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* block_sums,
                                cudaStream_t s, const int* skip = nullptr);
 int64_t scan_scratch_elems(int64_t n);
+int scan_launch_count(int64_t n);
 
 }  // namespace plb

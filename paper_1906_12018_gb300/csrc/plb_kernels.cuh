@@ -40,8 +40,13 @@ struct RoundCounters {
     int nA_saved;                 // active count of the current round (restored on fallback)
     int cur;                      // buffer parity holding L and the previous frontier
     long long T;                  // labels so far (graph mode)
-    long long lcap, fcap, hcap;   // buffer capacities (graph mode)
+    long long lcap, hcap;         // label and probe-index buffer capacities (graph mode)
+    long long fcap[2];            // new-frontier buffer capacity per parity (graph mode)
 };
+
+// RoundCounters::fallback: why a graph stopped (1: after the gather, a buffer
+// was too small; kStopBeforeGather: the candidate bound exceeds the frontier buffer).
+constexpr int kStopBeforeGather = 2;
 
 // Per-round statistics written on the device (graph mode).
 struct RoundStat {

@@ -1044,6 +1044,17 @@ __global__ void k_g_begin(RoundCounters* ctr) {
     ctr->d += 1;
 }
 
+// After the frontier step: stop before the gather when the round's candidate
+// bound (an upper bound on its new-frontier entries) exceeds the buffer of
+// parity x.
+__global__ void k_g_bound(RoundCounters* ctr, int x) {
+    if (ctr->done) return;
+    if ((long long)ctr->bound_sum > ctr->fcap[x]) {
+        ctr->fallback = kStopBeforeGather;
+        ctr->done = 1;
+    }
+}
+
 // After the gather/prune kernels: stop on a capacity problem (resume on the
 // host), on an empty round (finished) or on a distance above 254; else
 // account the new labels and record the round's statistics.

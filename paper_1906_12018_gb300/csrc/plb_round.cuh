@@ -33,6 +33,7 @@ __global__ void k_index_build(const int64_t* loff, const uint32_t* lent, const i
                               int64_t n, const RoundCounters* ctr);
 __global__ void k_set_round(RoundCounters* ctr, uint32_t d);
 __global__ void k_g_begin(RoundCounters* ctr);
+__global__ void k_g_bound(RoundCounters* ctr, int x);
 __global__ void k_g_check(RoundCounters* ctr, RoundStat* stats);
 __global__ void k_g_finish(RoundCounters* ctr);
 __global__ void k_g_cond(const RoundCounters* ctr, cudaGraphConditionalHandle h);

@@ -119,6 +119,12 @@ int64_t scan_scratch_elems(int64_t n) {
     return total + 1;
 }
 
+// Kernel launches of one exclusive_scan_i64 over n values.
+int scan_launch_count(int64_t n) {
+    if (n <= kTile) return 1;
+    return 3 + scan_launch_count((n + kTile - 1) / kTile);
+}
+
 // out[0..n] = exclusive scan of in[0..n), out[n] = sum.  With skip, every
 // kernel returns at once while *skip is non-zero (graph-driven rounds after
 // the loop has finished).

@@ -264,8 +264,9 @@ def test_graph_mode_bit_exact(rmat12):
 
 
 def test_graph_mode_capacity_fallback():
-    """K_1500 accepts 1.1M labels in round 1, more than the graph-mode label
-    capacity (2^20): the round is redone host-driven, labels unchanged."""
+    """K_1500 accepts 1.1M labels in round 1, more than the first graph-mode
+    label capacity (2^20): the buffers grow, the round is completed and the
+    graph resumes; labels unchanged."""
     n = 1500
     g = G.from_edges(n, [(i, j) for i in range(n) for j in range(i + 1, n)])
     order = np.arange(n, dtype=np.int32)
@@ -273,6 +274,24 @@ def test_graph_mode_capacity_fallback():
     assert lab.total == n * (n + 1) // 2
     assert lab.stats()["reruns"] >= 1
     assert_labels_equal(lab, O.pll(g.off, g.col, order), "K1500")
+
+
+def test_graph_mode_capacity_mid_build():
+    """A star of 1536 leaves whose centre is ranked last: round 1 gives the
+    centre every leaf (1536 labels), round 2 gives every leaf each higher
+    ranked leaf at distance 2 (any witness path is 4 long), 1.18M labels,
+    which stops the graph in round 2; it resumes with round 3."""
+    leaves = 1536
+    n = leaves + 1
+    g = G.from_edges(n, [(i, leaves) for i in range(leaves)])
+    order = np.arange(n, dtype=np.int32)
+    lab = gpu_build(g, order, use_graph=1)
+    pairs = leaves * (leaves - 1) // 2
+    assert lab.total == n + leaves + pairs
+    st = lab.stats()
+    assert st["reruns"] >= 1 and lab.rounds == gpu_build(g, order).rounds
+    assert st["accepted"][:2] == [leaves, pairs]
+    assert_labels_equal(lab, O.pll(g.off, g.col, order), "star, centre last")
 
 
 def test_graph_mode_distance_overflow():
