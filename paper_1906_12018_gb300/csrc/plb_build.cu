@@ -208,6 +208,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int32_t* A = pool.alloc<int32_t>(n);
     int32_t* R = pool.alloc<int32_t>(n);
     int32_t* O1 = pool.alloc<int32_t>(n);
+    uint32_t* rbound = pool.alloc<uint32_t>(n);
     int64_t* aoff = pool.alloc<int64_t>(n + 1);
     PLB_ALLOC_OK();
     PLB_CK(cudaMemsetAsync(recv, 0, sizeof(unsigned long long) * std::max<int64_t>(n, 1), s));
@@ -307,6 +308,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.top = top;
         p.gscratch = gacc;
         p.gscratch_words = std::max<int64_t>(n, 1);
+        p.rbound = rbound;
         return p;
     };
     const int* skip = nullptr;  // graph mode: &ctr->done (scans of finished rounds do nothing)
@@ -315,7 +317,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         cudaError_t e = exclusive_scan_i64(tmp64, aoff, n, scan_scr, s, skip);
         if (e != cudaSuccess) return e;
         k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[c], fhub[c], A, aoff, ctr, recv, n);
-        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[c], n, fse[x], R, O1, ctr, lim);
+        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[c], n, fse[x], R, O1, rbound, ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(ctr);
         st.launches += 4 + scan_n;
         return cudaGetLastError();

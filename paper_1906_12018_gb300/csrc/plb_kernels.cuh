@@ -75,6 +75,7 @@ struct GpParams {
     const int64_t* hoff;       // probe index of L: per row a hub-keyed table (empty rows: none)
     const uint32_t* htab;
     const uint32_t* top;       // per vertex: top-hub masks by distance level (see kTopHubs)
+    const uint32_t* rbound;    // per receiver: candidate bound min(v, messages)
 };
 
 // Witness prefilter: for the kTopHubs highest-ranked hubs, every vertex x

@@ -173,10 +173,12 @@ __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t*
 }
 
 // Receivers (recv[v] > 0) are routed by the candidate bound min(v, recv[v]),
-// |L(v)| and degree: warp tier (R) or block tier (O1).
-// Also clears recv and the new frontier descriptors, and sums the bounds.
+// |L(v)| and degree: warp tier (R) or block tier (O1); the bound is kept in
+// rbound[v] (it sizes the warp tier's tables).  Also clears recv and the new
+// frontier descriptors, and sums the bounds.
 __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const int64_t* loff, int64_t n,
-                          uint64_t* fse_new, int32_t* R, int32_t* O1, RoundCounters* ctr, TierLimits lim) {
+                          uint64_t* fse_new, int32_t* R, int32_t* O1, uint32_t* rbound, RoundCounters* ctr,
+                          TierLimits lim) {
     if (ctr->done) return;
     unsigned long long bsum = 0;
     const int lane = lane_id();
@@ -188,6 +190,7 @@ __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const i
             recv[v] = 0;
             const unsigned long long bound = c < (unsigned long long)v ? c : (unsigned long long)v;
             bsum += bound;
+            rbound[v] = (uint32_t)bound;  // v < 2^24
             const int64_t ll = loff[v + 1] - loff[v];
             const int64_t deg = roff[v + 1] - roff[v];
             tier = ((int64_t)bound <= lim.warp_bound && ll <= lim.warp_label && deg <= lim.warp_deg) ? 0 : 1;
@@ -371,12 +374,15 @@ __device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int6
         int c = 0;
         int64_t st = 0;
         if (j < ne) {
-            const uint64_t f = p.fse[p.rcol[j]];
+            const int32_t a = p.rcol[j];
+            const uint64_t f = p.fse[a];
             const uint32_t n0 = fcount(f);
             if (n0) {
+                // the hubs of dL_{d-1}(a) are <= a (a itself only for d = 1):
+                // for a < hi the whole row lies below hi
                 const uint32_t* row = p.fhub + fstart(f);
                 const int64_t a0 = lo ? lower_bound_u32(row, n0, lo) : 0;
-                const int64_t a1 = lower_bound_u32(row, n0, hi);
+                const int64_t a1 = (uint32_t)a < hi ? (int64_t)n0 : lower_bound_u32(row, n0, hi);
                 st = (int64_t)fstart(f) + a0;
                 c = (int)(a1 - a0);
             }
@@ -390,16 +396,16 @@ __device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int6
             const int k = warp_owner(excl, it);
             const int64_t stk = __shfl_sync(kFull, st, k);
             const int exk = __shfl_sync(kFull, excl, k);
+            bool ins = false;
             if (it < total) {
                 const uint32_t h = p.fhub[stk + (it - exk)];
                 if (!M || map_find(M, log_m, h) == kEmpty) {
-                    if (*(volatile int*)cnt_sm >= limit) {
-                        *ovf_sm = 1;
-                    } else if (set_insert(S, log_s, h)) {
-                        atomicAdd(cnt_sm, 1);
-                    }
+                    if (*(volatile int*)cnt_sm >= limit) *ovf_sm = 1;
+                    else ins = set_insert(S, log_s, h);
                 }
             }
+            const unsigned bm = __ballot_sync(kFull, ins);
+            if (lane == 0 && bm) atomicAdd(cnt_sm, __popc(bm));
             if (__any_sync(kFull, *ovf_sm != 0)) return false;
         }
     }
@@ -496,12 +502,15 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
         int c = 0;
         int64_t st = 0;
         if (j < ne) {
-            const uint64_t f = p.fse[p.rcol[j]];
+            const int32_t a = p.rcol[j];
+            const uint64_t f = p.fse[a];
             const uint32_t n0 = fcount(f);
             if (n0) {
+                // the hubs of dL_{d-1}(a) are <= a (a itself only for d = 1):
+                // for a < hi the whole row lies below hi
                 const uint32_t* row = p.fhub + fstart(f);
                 const int64_t a0 = lo ? lower_bound_u32(row, n0, lo) : 0;
-                const int64_t a1 = lower_bound_u32(row, n0, hi);
+                const int64_t a1 = (uint32_t)a < hi ? (int64_t)n0 : lower_bound_u32(row, n0, hi);
                 st = (int64_t)fstart(f) + a0;
                 c = (int)(a1 - a0);
             }
@@ -512,26 +521,35 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
         sst[tid] = st;
         if (tid == 0) sex[nthr] = total;
         __syncthreads();
-        const int per = (total + nthr - 1) / nthr;
-        const int beg = tid * per, end = min(total, beg + per);
-        if (beg < end) {
-            int k = 0, hk = nthr - 1;  // largest k with sex[k] <= beg
-            while (k < hk) {
-                const int mid = (k + hk + 1) >> 1;
-                if (sex[mid] <= beg) k = mid; else hk = mid - 1;
+        // each warp takes a contiguous range of the tile's messages, its lanes
+        // interleaved over it (lane j: items j, j + 32, ...), so that the
+        // lanes of a load read consecutive hubs of one frontier row
+        const int nw = nthr >> 5, lane = tid & 31;
+        const int per_w = (((total + nw - 1) / nw) + 31) & ~31;
+        const int wbeg = (tid >> 5) * per_w, wend = min(total, wbeg + per_w);
+        if (wbeg < wend) {
+            int it = wbeg + lane;
+            int k = 0, hk = nthr - 1;  // owner of it: largest k with sex[k] <= it
+            if (it < wend) {
+                while (k < hk) {
+                    const int mid = (k + hk + 1) >> 1;
+                    if (sex[mid] <= it) k = mid; else hk = mid - 1;
+                }
             }
-            for (int it = beg; it < end; ++it) {
-                while (it >= sex[k + 1]) ++k;
-                const uint32_t h = p.fhub[sst[k] + (it - sex[k])];
-                if (!M || map_find(M, log_m, h) == kEmpty) {
-                    if (*(volatile int*)cnt_sm >= limit) {
-                        *ovf_sm = 1;
-                        break;
-                    } else if (set_insert(S, log_s, h)) {
-                        atomicAdd(cnt_sm, 1);
+            const int niter = (wend - wbeg + 31) >> 5;
+            for (int i = 0; i < niter; ++i, it += 32) {
+                bool ins = false;
+                if (it < wend) {
+                    while (it >= sex[k + 1]) ++k;
+                    const uint32_t h = p.fhub[sst[k] + (it - sex[k])];
+                    if (!M || map_find(M, log_m, h) == kEmpty) {
+                        if (*(volatile int*)cnt_sm >= limit) *ovf_sm = 1;
+                        else ins = set_insert(S, log_s, h);
                     }
                 }
-                if (*ovf_sm) break;
+                const unsigned bm = __ballot_sync(kFull, ins);
+                if (lane == 0 && bm) atomicAdd(cnt_sm, __popc(bm));
+                if (__any_sync(kFull, *ovf_sm != 0)) break;
             }
         }
         if (tid == 0) msgs += total;
@@ -571,17 +589,22 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
         __syncwarp();
         const int32_t v = p.list[i];
         const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
-        for (int s = lane; s < S_CAP; s += 32) S[s] = kEmpty;
-        for (int s = lane; s < M_CAP; s += 32) M[s] = kEmpty;
+        // tables sized for this vertex: the set for its candidate bound (when
+        // within the tier's limit), the map for |L(v)| (load <= 1/2)
+        const uint32_t bnd = p.rbound[v];
+        const int log_s = bnd <= (uint32_t)p.cand_limit ? max(5, ceil_log2_i64(2 * (int64_t)bnd)) : p.log_s;
+        const int log_m = max(5, ceil_log2_i64(2 * ll));
+        for (int s = lane; s < (1 << log_s); s += 32) S[s] = kEmpty;
+        for (int s = lane; s < (1 << log_m); s += 32) M[s] = kEmpty;
         if (lane == 0) {
             wsc[0] = 0;
             wsc[1] = 0;
         }
         __syncwarp();
-        for (int64_t j = lane; j < ll; j += 32) map_insert(M, p.log_m, p.lent[lb + j]);
+        for (int64_t j = lane; j < ll; j += 32) map_insert(M, log_m, p.lent[lb + j]);
         __syncwarp();
         const int64_t nb = p.roff[v], ne = p.roff[v + 1];
-        const bool ok = gather_range(p, nb, ne, 32, 0u, (uint32_t)v, S, p.log_s, M, p.log_m, p.cand_limit, &wsc[0],
+        const bool ok = gather_range(p, nb, ne, 32, 0u, (uint32_t)v, S, log_s, M, log_m, p.cand_limit, &wsc[0],
                                      (volatile int*)&wsc[1], c_msgs);
         __syncwarp();
         const int nS = *(volatile int*)&wsc[0];
@@ -600,7 +623,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
         }
         // compact the set in place (write position never passes the read position)
         int nc = 0;
-        for (int sb = 0; sb < S_CAP; sb += 32) {
+        for (int sb = 0; sb < (1 << log_s); sb += 32) {
             const uint32_t h = S[sb + lane];
             __syncwarp();
             const bool has = h != kEmpty;
@@ -611,14 +634,14 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
         __syncwarp();
         // distance checks, 32 candidates at a time; survivors compacted in place
         uint32_t* tv = tvs + wib * kTopRow;
-        stage_exact_levels(p.top, v, tv, lane, 32);
+        if (nc > 0) stage_exact_levels(p.top, v, tv, lane, 32);
         __syncwarp();
         int nacc = 0;
         for (int cb = 0; cb < nc; cb += 32) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p, d, M, p.log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3],
+            const unsigned okm = check_chunk(p, d, M, log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3],
                                              c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
