@@ -71,9 +71,9 @@ typedef struct {
     int32_t validate;          /* 1: check CSR and order on the device first (default 1) */
     int32_t warp_label_cap;    /* largest |L(v)| handled one-vertex-per-warp (default 512) */
     int32_t warp_cand_cap;     /* largest unique-candidate count per warp-vertex (default 512) */
-    int32_t block_label_cap;   /* largest |L(v)| handled one-vertex-per-block in shared memory */
-    int32_t block_cand_cap;    /* largest candidate count for the block tier */
-    int32_t block_threads;     /* threads of the block tier (multiple of 32, <= 1024) */
+    int32_t block_label_cap;   /* largest |L(v)| the block tier stages in shared memory (default 2048) */
+    int32_t block_cand_cap;    /* unique candidates per hub-range pass of the block tier (default 2048) */
+    int32_t block_threads;     /* threads of the block tier, 64..256, rounded down to a multiple of 32 (default 256) */
     int32_t use_graph;         /* 1: run the round loop as ONE captured CUDA graph with a
                                   device-side while condition (no per-round host sync);
                                   buffers get fixed capacities (32 labels per vertex, at

@@ -8,6 +8,7 @@ Knobs (``plb_options``):
                     shared-memory probe width of the warp tier);
   * block_threads   threads of the block tier;
   * block_cand_cap  candidates per hub-range pass of the block tier;
+  * block_label_cap |L(v)| the block tier stages in its shared-memory map;
   * use_graph       round loop as one captured CUDA graph (1) or host-driven (0).
 
 Coordinate descent from the defaults: each knob in turn takes the value with
@@ -26,8 +27,9 @@ SPACE = {
     "use_graph": [1, 0],
     "warp_cand_cap": [256, 512, 1024],
     "warp_label_cap": [256, 512, 1024],
-    "block_threads": [256, 512],
-    "block_cand_cap": [2048, 4096],
+    "block_threads": [128, 256],
+    "block_cand_cap": [1024, 2048, 4096],
+    "block_label_cap": [1024, 2048],
 }
 
 

@@ -110,9 +110,9 @@ void plb_default_options(plb_options* o) {
     o->validate = 1;
     o->warp_label_cap = 512;
     o->warp_cand_cap = 512;
-    o->block_label_cap = 4096;
-    o->block_cand_cap = 4096;
-    o->block_threads = 512;
+    o->block_label_cap = 2048;
+    o->block_cand_cap = 2048;
+    o->block_threads = 256;
     o->use_graph = 0;
     o->profile = 0;
 }
@@ -129,7 +129,7 @@ static int check_csr(const plb_csr* g, const int32_t* order) {
 static bool sane_options(const plb_options& o) {
     return o.warp_label_cap >= 1 && o.warp_label_cap <= 8192 && o.warp_cand_cap >= 1 && o.warp_cand_cap <= 4096 &&
            o.block_label_cap >= 1 && o.block_label_cap <= 16384 && o.block_cand_cap >= 1 &&
-           o.block_cand_cap <= 16384 && o.block_threads >= 64 && o.block_threads <= 1024;
+           o.block_cand_cap <= 16384 && o.block_threads >= 64 && o.block_threads <= 256;
 }
 
 static int empty_labels(plb_labels** out, cudaStream_t s) {

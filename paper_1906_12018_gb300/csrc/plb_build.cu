@@ -257,7 +257,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     const int warps_per_block = kGpWarpThreads / 32;
     const size_t w_smem = sizeof(uint32_t) * (4 * warps_per_block +
                                               (size_t)warps_per_block * (kTopRow + (1 << w_log_s) + (1 << w_log_m)));
-    const int bthr = std::min(512, std::max(64, (o.block_threads / 32) * 32));
+    const int bthr = std::min(256, std::max(64, (o.block_threads / 32) * 32));  // k_gp_block: <= 256 threads
     const int block_cand = pow2_at_least(std::max(bthr, o.block_cand_cap));
     const int b_log_s = ceil_log2_i64(2 * (int64_t)block_cand);
     const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);

@@ -780,7 +780,7 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(512, 1) k_gp_block(GpParams p) {
+__global__ void __launch_bounds__(256, 3) k_gp_block(GpParams p) {
     extern __shared__ uint32_t sm[];
     int* sh = reinterpret_cast<int*>(sm);
     int* wsum = sh + SH_WORDS;                                      // 33 ints (+ pad)
