@@ -252,18 +252,24 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     // tier geometry
     const int warp_cand = pow2_at_least(std::max(32, o.warp_cand_cap));
     const int warp_label = std::max(16, o.warp_label_cap);
-    const int w_log_s = ceil_log2_i64(2 * warp_cand);
+    // set tables: load <= 1/2 at the candidate limit, plus the inserts a gather
+    // step can make before it sees the count (kGatherUnroll x 32 per warp)
+    const int w_log_s = ceil_log2_i64(std::max<int64_t>(2 * warp_cand, warp_cand + 32 * kGatherUnroll));
     const int w_log_m = ceil_log2_i64(2 * warp_label);
     const int warps_per_block = kGpWarpThreads / 32;
     const size_t w_smem = sizeof(uint32_t) * (4 * warps_per_block +
                                               (size_t)warps_per_block * (kTopRow + (1 << w_log_s) + (1 << w_log_m)));
     const int bthr = std::min(256, std::max(64, (o.block_threads / 32) * 32));  // k_gp_block: <= 256 threads
     const int block_cand = pow2_at_least(std::max(bthr, o.block_cand_cap));
-    const int b_log_s = ceil_log2_i64(2 * (int64_t)block_cand);
+    const int b_log_s = ceil_log2_i64(std::max<int64_t>(std::max<int64_t>(2 * (int64_t)block_cand,
+                                                                           block_cand + (int64_t)kGatherUnroll * bthr),
+                                                          (int64_t)kByteStage * (bthr / 32)));
     const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);
-    // scalars (48) + warp sums (34) + prefix per thread + 64-bit row start per thread + tables
+    // scalars (48) + warp sums (34) + histogram (256) + top-hub masks + prefix per thread + 64-bit row
+    // start per thread + set (also kByteStage per warp of byte-map staging) + map + candidate list (limit + 32 per warp) + byte map
     const size_t b_smem = sizeof(uint32_t) * (48 + 34 + 256 + kTopRow + (size_t)((bthr + 2) & ~1) + 2 * (size_t)bthr +
-                                              (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) + block_cand);
+                                              (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) +
+                                              (size_t)(block_cand + bthr) + kByteHubs / 4);
     TierLimits lim;
     lim.warp_bound = 2 * (int64_t)warp_cand;
     lim.warp_label = warp_label;

@@ -89,6 +89,15 @@ constexpr int kTopWords = kTopHubs / 32;             // words per mask
 constexpr int kTopLevels = 7;                        // distance levels 1..7
 constexpr int kTopRow = kTopLevels * kTopWords;      // words per vertex
 
+// Messages each lane loads before inserting them (gathers keep several loads
+// in flight per warp).
+constexpr int kGatherUnroll = 4;
+
+// Block tier: hubs below this rank are deduplicated in a shared-memory byte
+// map (one byte per hub) instead of the hash set.
+constexpr int kByteHubs = 8192;
+constexpr int kByteStage = 160;  // per-warp staging of byte-map candidates (< 32 carried + 128 new)
+
 // Rows of L with at least this many entries get a hub-keyed probe table.
 constexpr int kIndexMinLen = 16;
 

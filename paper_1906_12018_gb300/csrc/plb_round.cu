@@ -238,14 +238,8 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
 }
 
 // ------------------------------------------------------- gather + prune
-// Distance of hub w in the sorted label row r[0..len), or kEmpty.
-__device__ __forceinline__ uint32_t row_find(const uint32_t* r, int64_t len, uint32_t w) {
-    const int64_t i = lower_bound_u32(r, len, pack(w, 0));
-    if (i < len && hub_of(r[i]) == w) return dist_of(r[i]);
-    return kEmpty;
-}
-
 constexpr int kPrefilterMinItems = 12;  // prefilter only candidates with longer checks
+constexpr int kSideBMinItems = 16;      // shorter L(h) rows are always scanned (side A)
 
 // Top-hub witness prefilter for the 32 candidates of a chunk (one per lane):
 // candidate h has a witness among the kTopHubs highest-ranked hubs when
@@ -285,19 +279,21 @@ __device__ __forceinline__ void stage_exact_levels(const uint32_t* top, int32_t 
 // Distance check of up to 32 candidates held one per lane (valid lanes).
 // A witness for candidate h is a hub w of both v and h with
 // d(w,v) + d(w,h) <= d (the test of Alg. 3 with the labels of round d-1).
-// Each candidate scans the shorter side:
+// Each candidate scans one side:
 //   A: the entries of L(h) (its last entry, (h,0), is never a witness and is
-//      skipped), each looked up in L(v): in the shared-memory map M, or by
-//      binary search in the row lv when M is null;
+//      skipped), each looked up in the hub-keyed table M of L(v) (shared
+//      memory, or v's row of the global probe index when mv_global);
 //   B: the entries of L(v) with hub < h (only those can be hubs of h), each
 //      probed in h's row of the global probe index (rows of >= 16 entries).
-// All (candidate, entry) pairs are spread over the lanes; a candidate's
-// remaining entries are skipped once it has a witness.  Returns the lanes
-// whose candidate survives.
+// B is considered only for |L(h)| >= kSideBMinItems (the count of L(v)'s hubs
+// below h is a binary search), and taken when it is the shorter scan (by half,
+// against a shared-memory M).  All (candidate, entry) pairs are spread over
+// the lanes; a candidate's remaining entries are skipped once it has a
+// witness.  Returns the lanes whose candidate survives.
 __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, const uint32_t* M, int log_m,
-                                                const uint32_t* lv, int64_t lvlen, uint32_t h, bool valid,
-                                                unsigned* pm_sm, unsigned long long& probed, const uint32_t* tv,
-                                                unsigned long long& prefiltered) {
+                                                bool mv_global, const uint32_t* lv, int64_t lvlen, uint32_t h,
+                                                bool valid, unsigned* pm_sm, unsigned long long& probed,
+                                                const uint32_t* tv, unsigned long long& prefiltered) {
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
@@ -306,13 +302,15 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
         const int la = (int)(p.loff[h + 1] - hb) - 1;
         base = hb;
         items = la;
-        const int64_t x0 = p.hoff[h], x1 = p.hoff[h + 1];
-        if (x1 > x0) {
-            const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
-            if (2 * lb < la || M == nullptr) {
-                items = lb;
-                base = x0;
-                meta = __ffs((int)(x1 - x0));  // log2 + 1
+        if (la >= kSideBMinItems) {
+            const int64_t x0 = p.hoff[h], x1 = p.hoff[h + 1];
+            if (x1 > x0) {
+                const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
+                if (mv_global ? lb < la : 2 * lb < la) {
+                    items = lb;
+                    base = x0;
+                    meta = __ffs((int)(x1 - x0));  // log2 + 1
+                }
             }
         }
     }
@@ -342,7 +340,7 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
             bool hit = false;
             if (mk == 0) {
                 const uint32_t x = p.lent[bk + j];
-                const uint32_t dv = M ? map_find(M, log_m, hub_of(x)) : row_find(lv, lvlen, hub_of(x));
+                const uint32_t dv = map_find(M, log_m, hub_of(x));
                 hit = dv != kEmpty && dv + dist_of(x) <= d;
             } else {
                 const uint32_t y = lv[j];
@@ -391,21 +389,27 @@ __device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int6
         const int total = __shfl_sync(kFull, incl, 31);
         const int excl = incl - c;
         msgs += (lane == 0) ? (unsigned long long)total : 0ull;
-        for (int ib = 0; ib < total; ib += 32) {
-            const int it = ib + lane;
-            const int k = warp_owner(excl, it);
-            const int64_t stk = __shfl_sync(kFull, st, k);
-            const int exk = __shfl_sync(kFull, excl, k);
-            bool ins = false;
-            if (it < total) {
-                const uint32_t h = p.fhub[stk + (it - exk)];
-                if (!M || map_find(M, log_m, h) == kEmpty) {
+        for (int ib = 0; ib < total; ib += 32 * kGatherUnroll) {
+            uint32_t hv[kGatherUnroll];
+#pragma unroll
+            for (int u = 0; u < kGatherUnroll; ++u) {
+                const int it = ib + 32 * u + lane;
+                const int k = warp_owner(excl, it);
+                const int64_t stk = __shfl_sync(kFull, st, k);
+                const int exk = __shfl_sync(kFull, excl, k);
+                hv[u] = it < total ? p.fhub[stk + (it - exk)] : kEmpty;
+            }
+            int nins = 0;
+#pragma unroll
+            for (int u = 0; u < kGatherUnroll; ++u) {
+                const uint32_t h = hv[u];
+                if (h != kEmpty && (!M || map_find(M, log_m, h) == kEmpty)) {
                     if (*(volatile int*)cnt_sm >= limit) *ovf_sm = 1;
-                    else ins = set_insert(S, log_s, h);
+                    else nins += set_insert(S, log_s, h) ? 1 : 0;
                 }
             }
-            const unsigned bm = __ballot_sync(kFull, ins);
-            if (lane == 0 && bm) atomicAdd(cnt_sm, __popc(bm));
+            nins = warp_sum(nins);
+            if (lane == 0 && nins) atomicAdd(cnt_sm, nins);
             if (__any_sync(kFull, *ovf_sm != 0)) return false;
         }
     }
@@ -484,16 +488,18 @@ __device__ void shrink_pass(uint32_t* S, int log_s, uint32_t* C, int limit, uint
     }
 }
 
-// Block-wide load-balanced gather of v's messages with hub in [lo, *hi_sm)
-// into S: neighbours are taken in tiles of blockDim; each thread finds its
+// Block-wide load-balanced gather of v's messages with hub in [lo, *hi_sm):
+// hubs below W are marked in the byte map B (plain stores: duplicates write
+// the same byte, and L(v)'s hubs are cleared afterwards), the others go into
+// the set S.  Neighbours are taken in tiles of blockDim; each thread finds its
 // neighbour's sub-range of dL_{d-1}(a) (binary searches in the sorted row), a
 // block-wide exclusive scan of the counts assigns every thread an equal,
 // contiguous share of the tile's messages.  When the set would exceed
-// `limit`, the range is shrunk (shrink_pass) and the current tile redone, so
-// messages gathered below the new bound are kept.
-__device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t lo, uint32_t* hi_sm, uint32_t* S,
-                             int log_s, const uint32_t* M, int log_m, int limit, int* cnt_sm, volatile int* ovf_sm,
-                             int* wsum, int* sex, int64_t* sst, uint32_t* C, int* hist, int* tmp,
+// `limit`, its range (hubs >= W) is shrunk (shrink_pass) and the current tile
+// redone, so messages gathered below the new bound are kept.
+__device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t lo, uint32_t* hi_sm, uint8_t* B,
+                             uint32_t W, uint32_t* S, int log_s, const uint32_t* M, int log_m, int limit, int* cnt_sm,
+                             volatile int* ovf_sm, int* wsum, int* sex, int64_t* sst, uint32_t* C, int* hist, int* tmp,
                              unsigned long long& msgs) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int64_t t0 = nb; t0 < ne;) {
@@ -515,48 +521,75 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
                 c = (int)(a1 - a0);
             }
         }
-        int total;
+        // message offsets of the tile's non-empty rows, compacted (rows cut
+        // to nothing by the hub range are common and would otherwise be
+        // stepped over item by item)
+        int total, nne;
         const int excl = block_excl_scan(c, wsum, &total);
-        sex[tid] = excl;
-        sst[tid] = st;
-        if (tid == 0) sex[nthr] = total;
         __syncthreads();
-        // each warp takes a contiguous range of the tile's messages, its lanes
-        // interleaved over it (lane j: items j, j + 32, ...), so that the
-        // lanes of a load read consecutive hubs of one frontier row
+        const int fidx = block_excl_scan(c > 0 ? 1 : 0, wsum, &nne);
+        if (c > 0) {
+            sex[fidx] = excl;
+            sst[fidx] = st;
+        }
+        if (tid == 0) sex[nne] = total;
+        __syncthreads();
+        // each warp takes a contiguous range of the tile's messages and walks
+        // it in windows of 32 rows: lane j holds the start of row k0 + j, and
+        // 32 consecutive messages at a time find their row by a warp-shuffle
+        // search, so that the lanes of a load read consecutive hubs of a row
         const int nw = nthr >> 5, lane = tid & 31;
         const int per_w = (((total + nw - 1) / nw) + 31) & ~31;
         const int wbeg = (tid >> 5) * per_w, wend = min(total, wbeg + per_w);
         if (wbeg < wend) {
-            int it = wbeg + lane;
-            int k = 0, hk = nthr - 1;  // owner of it: largest k with sex[k] <= it
-            if (it < wend) {
-                while (k < hk) {
-                    const int mid = (k + hk + 1) >> 1;
-                    if (sex[mid] <= it) k = mid; else hk = mid - 1;
-                }
+            int k0 = 0, hk = nne - 1;  // row of wbeg: largest k with sex[k] <= wbeg
+            while (k0 < hk) {
+                const int mid = (k0 + hk + 1) >> 1;
+                if (sex[mid] <= wbeg) k0 = mid; else hk = mid - 1;
             }
-            const int niter = (wend - wbeg + 31) >> 5;
-            for (int i = 0; i < niter; ++i, it += 32) {
-                bool ins = false;
-                if (it < wend) {
-                    while (it >= sex[k + 1]) ++k;
-                    const uint32_t h = p.fhub[sst[k] + (it - sex[k])];
-                    if (!M || map_find(M, log_m, h) == kEmpty) {
-                        if (*(volatile int*)cnt_sm >= limit) *ovf_sm = 1;
-                        else ins = set_insert(S, log_s, h);
+            bool stop = false;
+            for (int it0 = wbeg; it0 < wend && !stop; k0 += 32) {
+                const int kr = k0 + lane;
+                const int ex = kr < nne ? sex[kr] : total;
+                const int64_t stv = kr < nne ? sst[kr] : 0;
+                const int wcap = k0 + 32 < nne ? sex[k0 + 32] : total;
+                const int wend_w = min(wend, wcap);
+                for (int ib = it0; ib < wend_w; ib += 32 * kGatherUnroll) {
+                    uint32_t hv[kGatherUnroll];
+#pragma unroll
+                    for (int u = 0; u < kGatherUnroll; ++u) {
+                        const int it = ib + 32 * u + lane;
+                        const int kk = warp_owner(ex, it);
+                        const int exk = __shfl_sync(kFull, ex, kk);
+                        const int64_t stk = __shfl_sync(kFull, stv, kk);
+                        hv[u] = it < wend_w ? p.fhub[stk + (it - exk)] : kEmpty;
+                    }
+                    int nins = 0;
+#pragma unroll
+                    for (int u = 0; u < kGatherUnroll; ++u) {
+                        const uint32_t h = hv[u];
+                        if (h < W) {
+                            B[h] = 1;
+                        } else if (h != kEmpty && (!M || map_find(M, log_m, h) == kEmpty)) {
+                            if (*(volatile int*)cnt_sm >= limit) *ovf_sm = 1;
+                            else nins += set_insert(S, log_s, h) ? 1 : 0;
+                        }
+                    }
+                    nins = warp_sum(nins);
+                    if (lane == 0 && nins) atomicAdd(cnt_sm, nins);
+                    if (__any_sync(kFull, *ovf_sm != 0)) {
+                        stop = true;
+                        break;
                     }
                 }
-                const unsigned bm = __ballot_sync(kFull, ins);
-                if (lane == 0 && bm) atomicAdd(cnt_sm, __popc(bm));
-                if (__any_sync(kFull, *ovf_sm != 0)) break;
+                it0 = wend_w;
             }
         }
         if (tid == 0) msgs += total;
         __syncthreads();
         // concurrent inserts can pass the limit without raising the flag
         if (*ovf_sm || *(volatile int*)cnt_sm > limit) {
-            shrink_pass(S, log_s, C, limit, lo, hi_sm, cnt_sm, hist, tmp);
+            shrink_pass(S, log_s, C, limit, lo > W ? lo : W, hi_sm, cnt_sm, hist, tmp);  // S holds hubs >= W
             if (tid == 0) *ovf_sm = 0;
             __syncthreads();
             continue;  // redo this tile with the smaller range
@@ -641,7 +674,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p, d, M, log_m, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3],
+            const unsigned okm = check_chunk(p, d, M, log_m, false, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3],
                                              c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
@@ -685,8 +718,8 @@ enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_HI = 4, SH_TMP = 5, SH
 // the new frontier at the end.  L(v) is staged into the shared-memory map when it fits;
 // otherwise membership in L(v) is a binary search in its row.
 __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32_t* S, uint32_t* M, uint32_t* C,
-                                uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst, int* hist, uint32_t* tv,
-                                unsigned long long* cnt) {
+                                uint8_t* B, uint32_t* gacc, int* sh, int* wsum, int* sex, int64_t* sst, int* hist,
+                                uint32_t* tv, unsigned long long* cnt) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
     const int64_t lb = p.loff[v], ll = p.loff[v + 1] - lb;
@@ -696,7 +729,17 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
     int log_m = ceil_log2_i64(2 * ll + 2 * nthr);
     if (log_m < 5) log_m = 5;
     const bool useM = log_m <= p.log_m;
-    const uint32_t* Mp = useM ? M : nullptr;
+    // L(v) lookups: the shared-memory map, or v's row of the global probe
+    // index (a row too long for the map has more than 64 >= kIndexMinLen
+    // entries, so it is indexed)
+    static_assert(kIndexMinLen <= 64, "rows beyond the block map must be indexed");
+    const uint32_t* Mp = M;
+    int log_mp = log_m;
+    if (!useM) {
+        const int64_t x0 = p.hoff[v], x1 = p.hoff[v + 1];
+        Mp = p.htab + x0;
+        log_mp = __ffsll((unsigned long long)(x1 - x0)) - 1;
+    }
     if (useM) {
         for (int s = tid; s < (1 << log_m); s += nthr) M[s] = kEmpty;
         __syncthreads();
@@ -712,6 +755,12 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
     uint32_t lo = 0;
     int64_t width = v;
     uint32_t* hi_sm = reinterpret_cast<uint32_t*>(&sh[SH_HI]);
+    // hubs below W (the most frequent messages) are deduplicated in the byte
+    // map, in the first pass, for vertices with many messages (for the others
+    // clearing and scanning the map costs more than the hashing it saves)
+    const uint32_t W = p.rbound[v] >= (uint32_t)(kByteHubs / 4) ? min((uint32_t)kByteHubs, (uint32_t)v) : 0u;
+    const int nbw = (int)((W + 3) / 4);  // byte-map words in use
+    for (int q = tid; q < nbw; q += nthr) reinterpret_cast<uint32_t*>(B)[q] = 0u;
     while ((int64_t)lo < (int64_t)v) {
         for (int s = tid; s < S_CAP; s += nthr) S[s] = kEmpty;
         if (tid == 0) {
@@ -722,10 +771,16 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
             *hi_sm = (uint32_t)min((int64_t)v, (int64_t)lo + width);
         }
         __syncthreads();
-        gather_block(p, nb, ne, lo, hi_sm, S, log_s, Mp, log_m, limit, &sh[SH_UNIQ], (volatile int*)&sh[SH_OVF],
-                     wsum, sex, sst, C, hist, &sh[SH_TMP], cnt[1]);
+        gather_block(p, nb, ne, lo, hi_sm, B, W, S, log_s, useM ? M : nullptr, log_m, limit, &sh[SH_UNIQ],
+                     (volatile int*)&sh[SH_OVF], wsum, sex, sst, C, hist, &sh[SH_TMP], cnt[1]);
         __syncthreads();
         const uint32_t hi = *(volatile uint32_t*)hi_sm;
+        if (lo < W) {  // first pass: drop L(v)'s hubs from the byte map
+            for (int64_t j = tid; j < ll; j += nthr) {
+                const uint32_t w = hub_of(lv[j]);
+                if (w < W) B[w] = 0;
+            }
+        }
         // compact the set into C (any order)
         for (int sb = 32 * wid; sb < S_CAP; sb += 32 * nw) {
             const uint32_t h = S[sb + lane];
@@ -741,15 +796,61 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
             }
         }
         __syncthreads();
-        const int nc = min(*(volatile int*)&sh[SH_NC], limit);
-        if (tid == 0) cnt[2] += nc;
-        // distance checks: warp w takes candidate chunks w, w + nw, ...; the
+        const int nc_set = min(*(volatile int*)&sh[SH_NC], limit);  // candidates from the set
+        if (tid == 0) cnt[2] += nc_set;
+        if (lo < W) {
+            // the byte-map candidates: each warp extracts 32 words (up to 128
+            // hubs) at a time into its slice of S (free after the compaction;
+            // kByteStage words per warp), checks them in full chunks of 32 and
+            // carries the remainder; its final remainder (< 32) joins C
+            uint32_t* stage = S + wid * kByteStage;
+            int f = 0;  // candidates staged
+            for (int g = 32 * wid; g < nbw; g += 32 * nw) {
+                const uint32_t x = g + lane < nbw ? reinterpret_cast<const uint32_t*>(B)[g + lane] : 0u;
+                const uint32_t b4 = (x & 1u) | ((x >> 7) & 2u) | ((x >> 14) & 4u) | ((x >> 21) & 8u);
+                const int c = __popc(b4);
+                const int incl = warp_incl_scan(c, lane);
+                const int tot = __shfl_sync(kFull, incl, 31);
+                int o = f + incl - c;
+                for (int b = 0; b < 4; ++b)
+                    if ((b4 >> b) & 1u) stage[o++] = 4u * (uint32_t)(g + lane) + (uint32_t)b;
+                if (lane == 0) cnt[2] += tot;
+                f += tot;
+                __syncwarp();
+                const int nchk = f & ~31;
+                for (int cb = 0; cb < nchk; cb += 32) {
+                    const uint32_t h = stage[cb + lane];
+                    const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, lv, ll, h, true,
+                                                     (unsigned*)&sh[SH_PM + wid], cnt[4], tv, cnt[7]);
+                    int base = 0;
+                    if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
+                    base = __shfl_sync(kFull, base, 0);
+                    if ((okm >> lane) & 1u) gacc[total_acc + base + __popc(okm & ((1u << lane) - 1u))] = h;
+                }
+                const int rem = f - nchk;
+                uint32_t carry = 0u;
+                if (lane < rem) carry = stage[nchk + lane];
+                __syncwarp();
+                if (lane < rem) stage[lane] = carry;
+                f = rem;
+                __syncwarp();
+            }
+            int base = 0;
+            if (lane == 0 && f) base = atomicAdd(&sh[SH_NC], f);
+            base = __shfl_sync(kFull, base, 0);
+            if (lane < f) C[base + lane] = stage[lane];  // C holds limit + 32 per warp
+            __syncthreads();
+        }
+        // distance checks of C (the set's candidates, then the byte map's
+        // remainders): warp w takes candidate chunks w, w + nw, ...; the
         // survivors are appended (unsorted) to this block's scratch
+        const int nc = *(volatile int*)&sh[SH_NC];
         for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
             bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
-            if (!useM && valid && row_find(lv, ll, h) != kEmpty) valid = false;  // already a hub of v
-            const unsigned okm = check_chunk(p, d, Mp, log_m, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid],
+            // without the map, set candidates may be hubs of v already
+            if (!useM && valid && cb + lane < nc_set && map_find(Mp, log_mp, h) != kEmpty) valid = false;
+            const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid],
                                              cnt[4], tv, cnt[7]);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
@@ -791,25 +892,26 @@ __global__ void __launch_bounds__(256, 3) k_gp_block(GpParams p) {
     uint32_t* S = reinterpret_cast<uint32_t*>(sst + blockDim.x);
     uint32_t* M = S + (1 << p.log_s);
     uint32_t* C = M + (1 << p.log_m);
+    uint8_t* B = reinterpret_cast<uint8_t*>(C + p.cand_limit + (int)blockDim.x);  // kByteHubs bytes
     uint32_t* gacc = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
     unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (p.ctr->done) return;
     const uint32_t d = p.ctr->d;
     const int n1 = *p.list_n;
     for (int i = blockIdx.x; i < n1; i += gridDim.x) {
-        gp_block_vertex(p, d, p.list[i], S, M, C, gacc, sh, wsum, sex, sst, hist, tv, cnt);
+        gp_block_vertex(p, d, p.list[i], S, M, C, B, gacc, sh, wsum, sex, sst, hist, tv, cnt);
         __syncthreads();
     }
     cnt[1] = warp_sum(cnt[1]);
     cnt[4] = warp_sum(cnt[4]);
-    if ((threadIdx.x & 31) == 0) {
+    if ((threadIdx.x & 31) == 0) {  // lane 0 of each warp holds its warp's unique and prefiltered counts
         atomicAdd(&p.ctr->msgs, cnt[1]);
         atomicAdd(&p.ctr->probed, cnt[4]);
         atomicAdd(&p.ctr->prefiltered, cnt[7]);
+        atomicAdd(&p.ctr->uniq, cnt[2]);
     }
     if (threadIdx.x == 0) {
         atomicAdd(&p.ctr->arcs, cnt[0]);
-        atomicAdd(&p.ctr->uniq, cnt[2]);
         atomicAdd(&p.ctr->staged, cnt[3]);
         atomicAdd(&p.ctr->accepted, cnt[5]);
         atomicAdd(&p.ctr->tier[1], cnt[6]);
