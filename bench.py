@@ -48,6 +48,36 @@ def gather_prune_bytes(st: dict, n: int) -> int:
             + BYTES_PER_ACCEPTED * (st["total_labels"] - n))
 
 
+# DRAM traffic of the gather + prune kernels, from an ncu capture summarised in
+# profiles/ (valid only while the kernel sources hash to the recorded value).
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "gp_traffic_chunglu20.md")
+KERNEL_SOURCES = ("paper_1906_12018_gb300/csrc/plb_round.cu", "paper_1906_12018_gb300/csrc/plb_kernels.cuh",
+                  "paper_1906_12018_gb300/csrc/plb_internal.cuh")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload: str):
+    """(DRAM bytes per gather+prune launch, launches captured) recorded for
+    this workload, or None when there is no record or the kernels changed."""
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            rec = dict(line.strip()[2:].split(": ", 1) for line in f if line.startswith("- ") and ": " in line)
+    except OSError:
+        return None
+    if rec.get("workload") != workload or rec.get("kernel_sources_sha256") != kernel_source_hash():
+        return None
+    return float(rec["dram_bytes_per_launch"]), int(rec["launches"])
+
+
 def measured_peaks() -> tuple[float, str]:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -402,6 +432,8 @@ def main():
     st = lab.stats()
     gp_ms = sum(st["ms_gather_prune"])
     gp_bytes = gather_prune_bytes(st, g.n)
+    gp_launches = 2 * st["rounds"]  # both tiers, every round
+    traffic = recorded_traffic(args.workload)
     peak, peak_kind = measured_peaks()
     achieved = gp_bytes / (gp_ms / 1e3) / 1e9 if gp_ms > 0 else 0.0
 
@@ -477,7 +509,10 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "gather+prune (k_gp_warp + k_gp_block)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
-                         "traffic": None, "algorithmic_bytes": gp_bytes, "kernel_ms": gp_ms,
+                         "traffic": traffic[0] if traffic else None,
+                         "traffic_unit": "DRAM bytes per launch (ncu, profiles/gp_traffic_chunglu20.md)",
+                         "algorithmic_bytes_per_launch": gp_bytes / gp_launches, "launches_per_build": gp_launches,
+                         "algorithmic_bytes": gp_bytes, "kernel_ms": gp_ms,
                          "build_ms_profiled": st["ms_total"]},
             "kernel_ms": {"prepare": st["ms_prepare"], "frontier": st["ms_frontier"],
                           "gather_prune": st["ms_gather_prune"][:2], "merge_sort_index": st["ms_merge"],

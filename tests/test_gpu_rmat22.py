@@ -1,0 +1,82 @@
+"""R-MAT scale 22 (edge factor 16, seed 3, LCC: 2.39M vertices, 64.2M edges,
+1.8G labels), the serving workload, at full size with the default launch
+configuration: sampled rows against Def. 2, sampled queries against BFS, and
+the row invariants over every label (checked on the device, in slices)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from gpu_util import gpu_build, gpu_query  # noqa: E402
+from paper_1906_12018_gb300 import graphs as G  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rmat22():
+    g = G.workload("rmat22")
+    order = G.degree_order(g)
+    lab = gpu_build(g, order)
+    yield g, order, lab
+    lab.free()
+    torch.cuda.empty_cache()
+
+
+def test_rmat22_size(rmat22):
+    g, order, lab = rmat22
+    assert (g.n, g.m) == (2394833, 64152981)
+    assert lab.total == 1799946086
+
+
+def test_rmat22_sampled_rows_match_definition(rmat22):
+    g, order, lab = rmat22
+    off_d, hub_d, dist_d = lab.device_arrays()
+    off = off_d.cpu().numpy()
+    rng = np.random.default_rng(22)
+    deg = g.degrees()
+    picks = list(rng.choice(g.n, 10, replace=False)) + list(order[:3]) + list(np.argsort(-deg)[500:503])
+    for v in picks:
+        h, d = O.chhl_row(g.off, g.col, order, int(v))
+        a, b = int(off[v]), int(off[v + 1])
+        assert np.array_equal(hub_d[a:b].cpu().numpy().astype(np.uint32), h), v
+        assert np.array_equal(dist_d[a:b].cpu().numpy(), d), v
+
+
+def test_rmat22_sampled_queries_match_bfs(rmat22):
+    g, order, lab = rmat22
+    rng = np.random.default_rng(23)
+    srcs = rng.choice(g.n, 3, replace=False)
+    pairs = np.concatenate([np.stack([np.full(1000, s), rng.choice(g.n, 1000, replace=False)], 1)
+                            for s in srcs]).astype(np.int32)
+    got = gpu_query(lab, pairs)
+    for i, s in enumerate(srcs):
+        D = O.bfs(g.off, g.col, int(s))
+        assert np.array_equal(got[i * 1000:(i + 1) * 1000], D[pairs[i * 1000:(i + 1) * 1000, 1]])
+
+
+def test_rmat22_invariants_all_rows(rmat22):
+    """(v, 0) closes every row, hubs outrank their row's vertex, rows strictly
+    increase: over all 1.8G labels."""
+    g, order, lab = rmat22
+    off, hub, dist = lab.device_arrays()
+    dev = off.device
+    rank = torch.empty(g.n, dtype=torch.int64, device=dev)
+    rank[torch.from_numpy(order.astype(np.int64)).to(dev)] = torch.arange(g.n, device=dev)
+    last = off[1:] - 1
+    assert bool(torch.all(off[1:] > off[:-1]))
+    assert torch.equal(hub[last].long(), rank)
+    assert bool(torch.all(dist[last] == 0))
+    step = 1 << 27
+    for a in range(0, lab.total, step):
+        a = max(a - 1, 0)  # slices overlap by one entry: every adjacent pair is compared
+        b = min(lab.total, a + 1 + step)
+        q = torch.arange(a, b, device=dev)
+        r = torch.searchsorted(off, q, right=True) - 1      # row of each entry
+        assert bool(torch.all(hub[a:b].long() <= rank[r]))   # hierarchy
+        if b - a > 1:
+            same = r[1:] == r[:-1]
+            inc = hub[a + 1:b].long() > hub[a:b - 1].long()
+            assert bool(torch.all(inc | ~same))              # strictly increasing within rows
+        del q, r
