@@ -379,52 +379,69 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         ++d;
         const int nxt = cur ^ 1;
         cudaEvent_t r0 = tm.on ? tm.mark() : nullptr;
-        if (!frontier_done) {
-            k_set_round<<<1, 1, 0, s>>>(ctr, (uint32_t)d);
-            st.launches += 1;
-            // frontier: mark receivers from the active list, collect them
-            PLB_CK(launch_frontier(cur, nxt));
-        }
-        // size the new frontier buffer from the candidate bound (no re-run)
-        PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
-        PLB_CK(cudaStreamSynchronize(s));
-        if ((int64_t)hctr->bound_sum > fcap[nxt]) {
-            const int64_t want = std::min<int64_t>((int64_t)hctr->bound_sum + 1024,
-                                                   std::max<int64_t>(int64_t(1) << 31, 2 * fcap[nxt]));
-            if (want > fcap[nxt]) {
-                pool.release(fhub[nxt]);
-                fcap[nxt] = want;
-                fhub[nxt] = pool.alloc<uint32_t>(fcap[nxt]);
-                PLB_ALLOC_OK();
-            }
-        }
-        cudaEvent_t r1 = tm.on ? tm.mark() : nullptr;
-        if (tm.on) tm.span(T_FRONT, r0, r1);
-        bool rerun = false;
-        for (;;) {
-            if (rerun) {
-                k_rerun_reset<<<gflat, kFlatThreads, 0, s>>>(ctr, fse[nxt], n);
-                st.launches += 1;
-            }
-            cudaEvent_t g0 = tm.on ? tm.mark() : nullptr, g1 = nullptr;
-            PLB_CK(launch_gp(gp_params(cur, nxt, fcap[nxt]), tm.on ? &g1 : nullptr));
-            cudaEvent_t g2 = tm.on ? tm.mark() : nullptr;
-            if (tm.on) {
-                tm.span(T_GPW, g0, g1);
-                tm.span(T_GPB, g1, g2);
-            }
+        if (d == 1) {
+            // round 1 needs no frontier step and no check (k_round1); the
+            // new-frontier buffer holds every arc
+            k_set_round<<<1, 1, 0, s>>>(ctr, 1u);
+            k_round1<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
+                roff, rcol, n, fse[nxt], fhub[nxt], (unsigned long long)fcap[nxt], ctr);
+            st.launches += 2;
+            PLB_CK(cudaGetLastError());
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));
-            if (hctr->guard) return PLB_ERR_CUDA;
-            if (!hctr->fovf) break;
-            // new-frontier buffer too small: grow it and run the gather again
-            const int64_t need = (int64_t)hctr->cursor;
-            pool.release(fhub[nxt]);
-            fcap[nxt] = need + need / 2 + 1024;
-            fhub[nxt] = pool.alloc<uint32_t>(fcap[nxt]);
-            PLB_ALLOC_OK();
-            st.reruns += 1;
-            rerun = true;
+            if (hctr->fovf) return PLB_ERR_CUDA;
+            if (tm.on) {
+                cudaEvent_t r1 = tm.mark();
+                tm.span(T_GPW, r0, r1);
+            }
+        } else {
+            if (!frontier_done) {
+                k_set_round<<<1, 1, 0, s>>>(ctr, (uint32_t)d);
+                st.launches += 1;
+                // frontier: mark receivers from the active list, collect them
+                PLB_CK(launch_frontier(cur, nxt));
+            }
+            // size the new frontier buffer from the candidate bound (no re-run)
+            PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+            PLB_CK(cudaStreamSynchronize(s));
+            if ((int64_t)hctr->bound_sum > fcap[nxt]) {
+                const int64_t want = std::min<int64_t>((int64_t)hctr->bound_sum + 1024,
+                                                       std::max<int64_t>(int64_t(1) << 31, 2 * fcap[nxt]));
+                if (want > fcap[nxt]) {
+                    pool.release(fhub[nxt]);
+                    fcap[nxt] = want;
+                    fhub[nxt] = pool.alloc<uint32_t>(fcap[nxt]);
+                    PLB_ALLOC_OK();
+                }
+            }
+            cudaEvent_t r1 = tm.on ? tm.mark() : nullptr;
+            if (tm.on) tm.span(T_FRONT, r0, r1);
+            bool rerun = false;
+            for (;;) {
+                if (rerun) {
+                    k_rerun_reset<<<gflat, kFlatThreads, 0, s>>>(ctr, fse[nxt], n);
+                    st.launches += 1;
+                }
+                cudaEvent_t g0 = tm.on ? tm.mark() : nullptr, g1 = nullptr;
+                PLB_CK(launch_gp(gp_params(cur, nxt, fcap[nxt]), tm.on ? &g1 : nullptr));
+                cudaEvent_t g2 = tm.on ? tm.mark() : nullptr;
+                if (tm.on) {
+                    tm.span(T_GPW, g0, g1);
+                    tm.span(T_GPB, g1, g2);
+                }
+                PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+                PLB_CK(cudaStreamSynchronize(s));
+                if (hctr->guard) return PLB_ERR_CUDA;
+                if (!hctr->fovf) break;
+                // new-frontier buffer too small: grow it and run the gather again
+                const int64_t need = (int64_t)hctr->cursor;
+                pool.release(fhub[nxt]);
+                fcap[nxt] = need + need / 2 + 1024;
+                fhub[nxt] = pool.alloc<uint32_t>(fcap[nxt]);
+                PLB_ALLOC_OK();
+                st.reruns += 1;
+                rerun = true;
+            }
         }
         const int64_t acc = (int64_t)hctr->accepted;
         if (d < PLB_MAX_ROUNDS) {
@@ -490,7 +507,11 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     // continues host-driven), after it when its labels exceed the label buffers
     // (they grow and the round's merge runs here).  The graph is then captured
     // again and resumes with the next round.
-    if (o.use_graph) {
+    {  // round 1 is always host-driven (one kernel)
+        const int e = host_round(false);
+        if (e != PLB_OK) return e;
+    }
+    if (o.use_graph && !finished) {
         RoundStat* dstat = pool.alloc<RoundStat>(PLB_MAX_ROUNDS);
         PLB_ALLOC_OK();
         PLB_CK(cudaMemsetAsync(dstat, 0, sizeof(RoundStat) * PLB_MAX_ROUNDS, s));

@@ -1,17 +1,20 @@
 // Kernels of the vertex-centric labeling rounds (Alg. 3, Sec. 3.1), in rank
 // space: vertex i is the vertex of rank i, so "h outranks v" is h < v.
 //
-// Per round d (labels L and frontier dL_{d-1} as they stood after round d-1):
+// Round 1 is k_round1 (no candidate can be pruned).  Per round d >= 2
+// (labels L and frontier dL_{d-1} as they stood after round d-1):
 //   k_mark         every active a (dL_{d-1}(a) non-empty) flags the neighbours
 //                  v that some hub of dL_{d-1}(a) outranks (scatter, Alg. 3).
-//   k_collect      flagged vertices become this round's receivers; heavy ones
-//                  (large |L(v)| or degree) go straight to the block tier.
+//   k_collect      flagged vertices become this round's receivers, routed by
+//                  their candidate bound, |L(v)| and degree to a tier.
 //   k_gp_warp      gather + dedup + distance check, one vertex per warp, with
 //                  L(v) staged hub-keyed in shared memory (the gather of
 //                  Alg. 3: unique messages, then d < min over common hubs).
-//   k_gp_block     the same with one vertex per block (bigger tables).
-//   k_gp_global    the same with tables in global scratch (any size).
-//   k_merge_*      L(v) <- L(v) U dL_d(v), keeping rows sorted by hub rank.
+//   k_gp_block     the same with one vertex per block (any size: hub-range
+//                  passes, a byte map for the top hubs).
+//   k_sort_rows_*, k_merge_*
+//                  L(v) <- L(v) U dL_d(v), keeping rows sorted by hub rank;
+//                  then the probe index of L is rebuilt (k_index_*).
 #pragma once
 
 #include "plb_internal.cuh"

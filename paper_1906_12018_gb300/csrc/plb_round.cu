@@ -222,6 +222,78 @@ __global__ void k_after_collect(RoundCounters* ctr) {
     ctr->nA = 0;
 }
 
+// Round 1 (Alg. 3 with d = 1).  The candidates of v are its neighbours a < v
+// (each sends its only label (a, 0)), they are distinct, and none is pruned:
+// a witness w of (a, 1) at v would need d(w, v) + d(w, a) <= 1 with w in
+// L(v) = {(v, 0)} and in L(a) = {(a, 0)}, impossible for a != v.  So
+// dL_1(v) = {a in N(v) : a < v}: one warp per vertex appends it (unsorted;
+// the merge step sorts the rows), clears the other frontier descriptors and
+// restarts the active list.  Counted like the general round: one message,
+// one unique candidate and one accepted label per such neighbour.
+__global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, uint64_t* fse_new, uint32_t* fhub_new,
+                         unsigned long long fcap, RoundCounters* ctr) {
+    if (ctr->done) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->nA_saved = ctr->nA;
+        ctr->nA = 0;
+    }
+    const int lane = lane_id();
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long c_acc = 0, c_arcs = 0, c_recv = 0;
+    for (int64_t v = warp0; v < n; v += nwarps) {
+        const int64_t nb = roff[v], ne = roff[v + 1];
+        int c = 0;
+        for (int64_t j0 = nb; j0 < ne; j0 += 128) {  // four independent loads per lane
+            int k = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t j = j0 + 32 * u + lane;
+                k += (j < ne && rcol[j] < v) ? 1 : 0;
+            }
+            c += k;
+        }
+        c = warp_sum(c);
+        if (c == 0) {
+            if (lane == 0) fse_new[v] = 0;
+            continue;
+        }
+        unsigned long long start = 0;
+        if (lane == 0) start = atomicAdd(&ctr->cursor, (unsigned long long)c);
+        start = __shfl_sync(kFull, start, 0);
+        if (start + c > fcap) {  // cannot happen: the buffer holds every arc
+            if (lane == 0) {
+                ctr->fovf = 1;
+                fse_new[v] = 0;
+            }
+            continue;
+        }
+        int o = 0;
+        for (int64_t j0 = nb; j0 < ne; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const int32_t a = j < ne ? rcol[j] : INT32_MAX;
+            const bool up = a < v;
+            const unsigned m = __ballot_sync(kFull, up);
+            if (up) fhub_new[start + o + __popc(m & ((1u << lane) - 1u))] = (uint32_t)a;
+            o += __popc(m);
+        }
+        if (lane == 0) {
+            fse_new[v] = fpack(start, (uint32_t)c);
+            c_acc += c;
+            c_arcs += ne - nb;
+            c_recv += 1;
+        }
+    }
+    if (lane == 0 && c_recv) {
+        atomicAdd(&ctr->accepted, c_acc);
+        atomicAdd(&ctr->msgs, c_acc);
+        atomicAdd(&ctr->uniq, c_acc);
+        atomicAdd(&ctr->arcs, c_arcs);
+        atomicAdd(&ctr->tier[0], c_recv);
+        atomicAdd(&ctr->nR, (int)c_recv);
+    }
+}
+
 // Reset before re-running the gather/prune of a round with a bigger buffer.
 __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
