@@ -311,7 +311,10 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
 
 // ------------------------------------------------------- gather + prune
 constexpr int kPrefilterMinItems = 12;  // prefilter only candidates with longer checks
-constexpr int kSideBMinItems = 16;      // shorter L(h) rows are always scanned (side A)
+// Side B of the check (see check_chunk), per tier (measured: side B saves most
+// on power-law graphs with heavy hubs in both tiers).
+constexpr int kWarpSideBMin = 16, kWarpSideBShift = 1;
+constexpr int kBlockSideBMin = 16, kBlockSideBShift = 1;
 
 // Top-hub witness prefilter for the 32 candidates of a chunk (one per lane):
 // candidate h has a witness among the kTopHubs highest-ranked hubs when
@@ -357,15 +360,17 @@ __device__ __forceinline__ void stage_exact_levels(const uint32_t* top, int32_t 
 //      memory, or v's row of the global probe index when mv_global);
 //   B: the entries of L(v) with hub < h (only those can be hubs of h), each
 //      probed in h's row of the global probe index (rows of >= 16 entries).
-// B is considered only for |L(h)| >= kSideBMinItems (the count of L(v)'s hubs
-// below h is a binary search), and taken when it is the shorter scan (by half,
-// against a shared-memory M).  All (candidate, entry) pairs are spread over
+// B is considered only for |L(h)| >= b_min (the count of L(v)'s hubs below h
+// is a binary search in L(v)'s row) and taken when it is the shorter scan, by
+// a factor 2^b_shift against a shared-memory M (whose probes are cheaper
+// than the global table's).  All (candidate, entry) pairs are spread over
 // the lanes; a candidate's remaining entries are skipped once it has a
 // witness.  Returns the lanes whose candidate survives.
 __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, const uint32_t* M, int log_m,
-                                                bool mv_global, const uint32_t* lv, int64_t lvlen, uint32_t h,
-                                                bool valid, unsigned* pm_sm, unsigned long long& probed,
-                                                const uint32_t* tv, unsigned long long& prefiltered) {
+                                                bool mv_global, int b_min, int b_shift, const uint32_t* lv,
+                                                int64_t lvlen, uint32_t h, bool valid, unsigned* pm_sm,
+                                                unsigned long long& probed, const uint32_t* tv,
+                                                unsigned long long& prefiltered) {
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
@@ -374,11 +379,11 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
         const int la = (int)(p.loff[h + 1] - hb) - 1;
         base = hb;
         items = la;
-        if (la >= kSideBMinItems) {
+        if (la >= b_min) {
             const int64_t x0 = p.hoff[h], x1 = p.hoff[h + 1];
             if (x1 > x0) {
                 const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
-                if (mv_global ? lb < la : 2 * lb < la) {
+                if (mv_global ? lb < la : (lb << b_shift) < la) {
                     items = lb;
                     base = x0;
                     meta = __ffs((int)(x1 - x0));  // log2 + 1
@@ -746,7 +751,8 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p, d, M, log_m, false, p.lent + lb, ll, h, valid, (unsigned*)&wsc[3],
+            const unsigned okm = check_chunk(p, d, M, log_m, false, kWarpSideBMin, kWarpSideBShift, p.lent + lb, ll, h,
+                                             valid, (unsigned*)&wsc[3],
                                              c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
@@ -892,7 +898,8 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
                 const int nchk = f & ~31;
                 for (int cb = 0; cb < nchk; cb += 32) {
                     const uint32_t h = stage[cb + lane];
-                    const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, lv, ll, h, true,
+                    const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lv,
+                                                     ll, h, true,
                                                      (unsigned*)&sh[SH_PM + wid], cnt[4], tv, cnt[7]);
                     int base = 0;
                     if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
@@ -922,7 +929,8 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
             const uint32_t h = valid ? C[cb + lane] : 0u;
             // without the map, set candidates may be hubs of v already
             if (!useM && valid && cb + lane < nc_set && map_find(Mp, log_mp, h) != kEmpty) valid = false;
-            const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, lv, ll, h, valid, (unsigned*)&sh[SH_PM + wid],
+            const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lv, ll, h,
+                                             valid, (unsigned*)&sh[SH_PM + wid],
                                              cnt[4], tv, cnt[7]);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
