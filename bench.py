@@ -51,7 +51,7 @@ def gather_prune_bytes(st: dict, n: int) -> int:
 # DRAM traffic of the gather + prune kernels, from an ncu capture summarised in
 # profiles/ (valid only while the kernel sources hash to the recorded value).
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "gp_traffic_chunglu20.md")
-KERNEL_SOURCES = ("paper_1906_12018_gb300/csrc/plb_round.cu", "paper_1906_12018_gb300/csrc/plb_kernels.cuh",
+KERNEL_SOURCES = ("paper_1906_12018_gb300/csrc/plb_gather.cu", "paper_1906_12018_gb300/csrc/plb_kernels.cuh",
                   "paper_1906_12018_gb300/csrc/plb_internal.cuh")
 
 

@@ -1,4 +1,5 @@
-// Declarations of the round kernels (defined in plb_round.cu).
+// Declarations of the round kernels (plb_round.cu; the gather + prune kernels
+// k_gp_warp and k_gp_block in plb_gather.cu).
 #pragma once
 
 #include "plb_kernels.cuh"
@@ -29,9 +30,6 @@ __global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, ui
 __global__ void k_gp_warp(GpParams p);
 __global__ void k_gp_block(GpParams p);
 __global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const RoundCounters* ctr);
-__global__ void k_index_clear(uint32_t* htab, const int64_t* hoff_n);
-__global__ void k_index_fill(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
-                             int64_t n);
 __global__ void k_index_build(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
                               int64_t n, const RoundCounters* ctr);
 __global__ void k_set_round(RoundCounters* ctr, uint32_t d);
