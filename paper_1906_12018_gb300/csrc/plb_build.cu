@@ -228,7 +228,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     uint32_t* htab = pool.alloc<uint32_t>(hcap);
     PLB_ALLOC_OK();
     PLB_CK(cudaFuncSetAttribute(k_index_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(8 * 2048 * sizeof(uint32_t))));
+                                (int)(sizeof(uint32_t) * kIndexWarps * kIndexSmemSlotsMax)));
+    // shared-memory table buffer of k_index_build: 512 slots while the mean
+    // row is short (most tables fit and eight blocks share an SM), else 2048
+    auto index_slots = [&](int64_t total) { return total <= 128 * n ? 512 : kIndexSmemSlotsMax; };
     auto build_index = [&](int which, int64_t total) -> int {
         if (4 * total > hcap) {
             pool.release(htab);
@@ -238,8 +241,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
         k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[which], n, tmp64, ctr);
         if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
-        k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t), s>>>(
-            loff[which], lent[which], hoff, htab, n, ctr);
+        const int slots = index_slots(total);
+        k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), kIndexWarps * 32,
+                        sizeof(uint32_t) * kIndexWarps * slots, s>>>(loff[which], lent[which], hoff, htab, n, slots,
+                                                                     ctr);
         st.launches += 2 + scan_n;
         return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
     };
@@ -600,8 +605,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                     ce = exclusive_scan_i64(tmp64, hoff, n, scan_scr, s, skip);
                 }
                 if (ce == cudaSuccess) {
-                    k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), 256, 8 * 2048 * sizeof(uint32_t),
-                                    s>>>(loff[x], lent[x], hoff, htab, n, ctr);
+                    const int slots = index_slots(T);  // from the labels at capture time
+                    k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), kIndexWarps * 32,
+                                    sizeof(uint32_t) * kIndexWarps * slots, s>>>(loff[x], lent[x], hoff, htab, n,
+                                                                                 slots, ctr);
                     k_g_finish<<<1, 1, 0, s>>>(ctr);
                     st.launches += 6 + scan_n;  // loop control (4) and the index rebuild
                     ce = cudaGetLastError();

@@ -103,6 +103,12 @@ constexpr int kByteStage = 160;  // per-warp staging of byte-map candidates (< 3
 
 // Rows of L with at least this many entries get a hub-keyed probe table.
 constexpr int kIndexMinLen = 16;
+// k_index_build: warps per block, and the largest table a warp may build in
+// its shared-memory buffer (larger ones are filled in place).  The buffer is
+// chosen per launch: 512 slots (16 KB per block, eight blocks per SM) while
+// the rows are short, 2048 when they are long.
+constexpr int kIndexWarps = 8;
+constexpr int kIndexSmemSlotsMax = 2048;
 
 // Routing limits of k_collect (see the tier geometry in build_core).
 struct TierLimits {

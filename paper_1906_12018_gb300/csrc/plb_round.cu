@@ -321,18 +321,16 @@ __global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const
 }
 
 // One warp per indexed row: the table is built in shared memory (rows whose
-// table has up to kIndexSmemSlots slots) and written out whole, empty slots
+// table has up to `slots` slots) and written out whole, empty slots
 // included; larger tables are cleared and filled in place with atomics.
-constexpr int kIndexWarps = 8;
-constexpr int kIndexSmemSlots = 2048;
 
 __global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t* loff, const uint32_t* lent,
                                                                   const int64_t* hoff, uint32_t* htab, int64_t n,
-                                                                  const RoundCounters* ctr) {
+                                                                  int slots, const RoundCounters* ctr) {
     extern __shared__ uint32_t ibuf[];
     if (ctr->done) return;
     const int lane = lane_id(), w = threadIdx.x >> 5;
-    uint32_t* buf = ibuf + w * kIndexSmemSlots;
+    uint32_t* buf = ibuf + w * slots;
     const int64_t nwarps = (int64_t)gridDim.x * kIndexWarps;
     for (int64_t base = ((int64_t)blockIdx.x * kIndexWarps + w) * 32; base < n; base += nwarps * 32) {
         const int64_t x = base + lane;
@@ -350,12 +348,12 @@ __global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t*
             const int Pk = (int)__shfl_sync(kFull, P, k);
             const int lg = __ffs(Pk) - 1;
             const int64_t lb = loff[xk], ll = loff[xk + 1] - lb;
-            uint32_t* tab = Pk <= kIndexSmemSlots ? buf : htab + hbk;
+            uint32_t* tab = Pk <= slots ? buf : htab + hbk;
             for (int sl = lane; sl < Pk; sl += 32) tab[sl] = kEmpty;
             __syncwarp();
             for (int64_t j = lane; j < ll; j += 32) map_insert(tab, lg, lent[lb + j]);
             __syncwarp();
-            if (Pk <= kIndexSmemSlots) {
+            if (Pk <= slots) {
                 for (int sl = lane; sl < Pk; sl += 32) htab[hbk + sl] = buf[sl];
                 __syncwarp();
             }

@@ -31,7 +31,7 @@ __global__ void k_gp_warp(GpParams p);
 __global__ void k_gp_block(GpParams p);
 __global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const RoundCounters* ctr);
 __global__ void k_index_build(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
-                              int64_t n, const RoundCounters* ctr);
+                              int64_t n, int slots, const RoundCounters* ctr);
 __global__ void k_set_round(RoundCounters* ctr, uint32_t d);
 __global__ void k_g_begin(RoundCounters* ctr);
 __global__ void k_g_bound(RoundCounters* ctr, int x);
