@@ -299,3 +299,30 @@ def test_graph_mode_distance_overflow():
     with pytest.raises(plb.PLBError) as e:
         gpu_build(g, np.arange(300, dtype=np.int32), use_graph=1)
     assert e.value.code == plb.PLB_ERR_DIST_OVERFLOW
+
+
+def test_largest_vertex_count():
+    """n = 2^24 - 1, the most vertices the 24-bit hub field admits: a double
+    star (centres 0 and 1 joined, leaf i on centre i mod 2).  Even leaves get
+    (0,1); odd leaves (1,1) in round 1 and (0,2) in round 2 (no hub common to
+    the leaf and 0 yet); every vertex its (v,0)."""
+    n = (1 << 24) - 1
+    leaves = np.arange(2, n, dtype=np.int32)
+    src = np.concatenate([np.array([0], np.int32), leaves])
+    dst = np.concatenate([np.array([1], np.int32), (leaves % 2).astype(np.int32)])
+    g = G.clean_csr(n, src, dst)
+    order = G.degree_order(g)
+    assert np.array_equal(order[:3], [0, 1, 2]) and order[-1] == n - 1
+    lab = gpu_build(g, order)
+    n_even, n_odd = (n - 1) // 2, (n - 2) // 2
+    assert lab.total == 1 + 2 + 2 * n_even + 3 * n_odd
+    assert lab.max_dist == 2 and lab.rounds == 3
+    off_d, hub_d, dist_d = lab.device_arrays()
+    for v, want in ((0, [(0, 0)]), (1, [(0, 1), (1, 0)]), (n - 1, [(0, 1), (n - 1, 0)]),
+                    (n - 2, [(0, 2), (1, 1), (n - 2, 0)])):
+        a, b = int(off_d[v]), int(off_d[v + 1])
+        got = list(zip(hub_d[a:b].cpu().numpy().astype(np.int64).tolist(), dist_d[a:b].cpu().numpy().tolist()))
+        assert got == want, (v, got)
+    pairs = np.array([[n - 1, n - 2], [n - 2, 3], [n - 1, 2], [n - 1, n - 1], [0, n - 2], [1, n - 1]], np.int32)
+    assert gpu_query(lab, pairs).tolist() == [3, 2, 2, 0, 2, 2]
+    lab.free()
