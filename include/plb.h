@@ -104,7 +104,7 @@ typedef struct {
 #define PLB_MAX_ROUNDS 256
 typedef struct {
     int32_t rounds;
-    int32_t reruns;                 /* rounds repeated after growing a scratch buffer */
+    int32_t reruns;                 /* gathers repeated after growing a buffer, and graph-mode stops */
     int64_t n, nnz, total_labels;
     /* per round d (index d, 1..rounds) */
     int64_t receivers[PLB_MAX_ROUNDS];   /* vertices that gathered messages */
@@ -112,16 +112,17 @@ typedef struct {
     int64_t unique_round[PLB_MAX_ROUNDS];  /* distinct candidates checked in round d */
     int64_t probed_round[PLB_MAX_ROUNDS];  /* label entries probed in distance checks in round d */
     int64_t prefiltered_round[PLB_MAX_ROUNDS]; /* candidates pruned by the top-hub witness prefilter */
-    int64_t messages_round[PLB_MAX_ROUNDS];/* frontier hubs read by the gather in round d */
+    int64_t messages_round[PLB_MAX_ROUNDS];/* frontier hubs h < v read by the gather in round d */
     double ms_round[PLB_MAX_ROUNDS];       /* device ms of round d (profile = 1 only) */
     /* totals over rounds */
     int64_t arcs_scanned;           /* neighbour entries read in the gather */
-    int64_t messages;               /* dL entries read by the gather (before dedup, before rank filter) */
+    int64_t messages;               /* frontier hubs h < v read by the gathers (before dedup) */
     int64_t unique_candidates;      /* distinct (h, v) pairs checked */
     int64_t staged_entries;         /* L(v) entries staged into the hub map */
-    int64_t probed_entries;         /* L(h) entries probed in distance checks */
-    int64_t tier_vertices[3];       /* vertex-rounds handled by warp / block / global tier */
+    int64_t probed_entries;         /* L(h) or L(v) entries probed in distance checks */
+    int64_t tier_vertices[3];       /* vertex-rounds: [0] round 1 and the warp tier, [1] block tier, [2] 0 */
     /* milliseconds on the device (profile = 1 only; else 0) */
+    /* ms_gather_prune: [0] round 1 and the warp tier, [1] block tier, [2] 0 */
     double ms_total, ms_prepare, ms_frontier, ms_gather_prune[3], ms_merge, ms_finalize;
     int64_t launches;               /* kernels launched by this build */
 } plb_build_stats;
