@@ -222,20 +222,28 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     PLB_ALLOC_OK();
     k_top_init<<<flat_grid_cap, kFlatThreads, 0, s>>>(top, n);
     st.launches += 1;
-    // probe index of L (hub-keyed table per long row), rebuilt after each merge
+    // probe index of L: a hub-keyed table per row of >= kIndexMinLen entries in
+    // a pool (htab), located by hdesc.  A full rebuild packs the tables and
+    // leaves room for growth; after each merge only the rows that changed are
+    // updated (new entries inserted, or a bigger table taken from the pool).
     int64_t* hoff = pool.alloc<int64_t>(n + 1);
+    uint64_t* hdesc = pool.alloc<uint64_t>(n);
     int64_t hcap = std::max<int64_t>(4 * n, 1024);
     uint32_t* htab = pool.alloc<uint32_t>(hcap);
     PLB_ALLOC_OK();
     PLB_CK(cudaFuncSetAttribute(k_index_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(uint32_t) * kIndexWarps * kIndexSmemSlotsMax)));
-    // shared-memory table buffer of k_index_build: 512 slots while the mean
+    PLB_CK(cudaFuncSetAttribute(k_index_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(uint32_t) * kIndexWarps * kIndexSmemSlotsMax)));
+    // shared-memory table buffer of the index kernels: 512 slots while the mean
     // row is short (most tables fit and eight blocks share an SM), else 2048
     auto index_slots = [&](int64_t total) { return total <= 128 * n ? 512 : kIndexSmemSlotsMax; };
     auto build_index = [&](int which, int64_t total) -> int {
-        if (4 * total > hcap) {
+        // packed tables take at most 4 |L| slots; keep as much again for growth
+        const int64_t want = 8 * total + 1024;
+        if (hcap < 6 * total + 1024) {
             pool.release(htab);
-            hcap = 4 * total + total / 2 + 1024;
+            hcap = want;
             htab = pool.alloc<uint32_t>(hcap);
             if (pool.failed) return PLB_ERR_OOM;
         }
@@ -243,10 +251,20 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
         const int slots = index_slots(total);
         k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), kIndexWarps * 32,
-                        sizeof(uint32_t) * kIndexWarps * slots, s>>>(loff[which], lent[which], hoff, htab, n, slots,
-                                                                     ctr);
-        st.launches += 2 + scan_n;
+                        sizeof(uint32_t) * kIndexWarps * slots, s>>>(loff[which], lent[which], hoff, htab, hdesc, n,
+                                                                     slots, ctr);
+        k_index_total<<<1, 1, 0, s>>>(hoff, n, ctr);
+        st.launches += 3 + scan_n;
         return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
+    };
+    // after a merge into parity c (labels and this round's frontier): update the
+    // rows that changed (the active list)
+    auto update_index = [&](int c, int64_t total) -> cudaError_t {
+        const int slots = index_slots(total);
+        k_index_update<<<flat_grid_cap, kIndexWarps * 32, sizeof(uint32_t) * kIndexWarps * slots, s>>>(
+            loff[c], lent[c], fse[c], fhub[c], A, htab, hdesc, (long long)hcap, slots, ctr);
+        st.launches += 1;
+        return cudaGetLastError();
     };
     {
         const int e = build_index(0, T);
@@ -314,7 +332,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.fhub_new = fhub[x];
         p.fcap = (unsigned long long)fc;
         p.ctr = ctr;
-        p.hoff = hoff;
+        p.hdesc = hdesc;
         p.htab = htab;
         p.top = top;
         p.gscratch = gacc;
@@ -409,6 +427,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             // size the new frontier buffer from the candidate bound (no re-run)
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));
+            if (hctr->hovf) {  // the last update did not fit the table pool: rebuild it, packed
+                const int e = build_index(cur, T);
+                if (e != PLB_OK) return e;
+            }
             if ((int64_t)hctr->bound_sum > fcap[nxt]) {
                 const int64_t want = std::min<int64_t>((int64_t)hctr->bound_sum + 1024,
                                                        std::max<int64_t>(int64_t(1) << 31, 2 * fcap[nxt]));
@@ -486,9 +508,11 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         PLB_CK(launch_merge(cur, nxt));
         T = Tn;
         cur = nxt;
-        {
+        if (d == 1) {  // most rows reach kIndexMinLen in round 1: a packed rebuild
             const int e = build_index(cur, T);
             if (e != PLB_OK) return e;
+        } else {
+            PLB_CK(update_index(cur, T));  // a table that did not fit shows up as hovf at the next sync
         }
         if (tm.on) tm.span(T_MERGE, m0, tm.mark());
         // round-start reset of the per-round counters (nA carries over)
@@ -534,12 +558,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         };
         for (int attempt = 0; attempt < 8 && !finished; ++attempt) {
             if (!grow(lent[cur], lcap[cur], lc, T) || !grow(lent[cur ^ 1], lcap[cur ^ 1], lc, 0)) return PLB_ERR_OOM;
-            if (4 * std::min(lcap[0], lcap[1]) > hcap) {
-                pool.release(htab);
-                hcap = 4 * std::min(lcap[0], lcap[1]);
-                htab = pool.alloc<uint32_t>(hcap);
-                PLB_ALLOC_OK();
-                const int e = build_index(cur, T);  // the current labels' index in the new table
+            {
+                const int e = build_index(cur, T);  // packed, with room for the segment's updates
                 if (e != PLB_OK) return e;
             }
             PLB_CK(cudaStreamSynchronize(s));
@@ -600,17 +620,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                     k_g_check<<<1, 1, 0, s>>>(ctr, dstat);
                     ce = launch_merge(c, x);
                 }
+                if (ce == cudaSuccess) ce = update_index(x, T);
                 if (ce == cudaSuccess) {
-                    k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[x], n, tmp64, ctr);
-                    ce = exclusive_scan_i64(tmp64, hoff, n, scan_scr, s, skip);
-                }
-                if (ce == cudaSuccess) {
-                    const int slots = index_slots(T);  // from the labels at capture time
-                    k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), kIndexWarps * 32,
-                                    sizeof(uint32_t) * kIndexWarps * slots, s>>>(loff[x], lent[x], hoff, htab, n,
-                                                                                 slots, ctr);
                     k_g_finish<<<1, 1, 0, s>>>(ctr);
-                    st.launches += 6 + scan_n;  // loop control (4) and the index rebuild
+                    st.launches += 4;  // loop control
                     ce = cudaGetLastError();
                 }
             }
@@ -648,6 +661,12 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             }
             st.reruns += 1;
             PLB_CK(cudaMemsetAsync(&ctr->done, 0, sizeof(int) * 2, s));
+            if (hctr->fallback == kStopIndex) {
+                // round dd is complete (parity flipped, counters reset); its probe
+                // index update did not fit: the next segment starts with a rebuild
+                d = dd;
+                continue;
+            }
             if (hctr->fallback == kStopBeforeGather) {
                 // round dd's candidate bound exceeds the new-frontier buffer:
                 // the round continues host-driven from its gather

@@ -84,13 +84,13 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
         base = hb;
         items = la;
         if (la >= b_min) {
-            const int64_t x0 = p.hoff[h], x1 = p.hoff[h + 1];
-            if (x1 > x0) {
+            const uint64_t hd = p.hdesc[h];
+            if (hd) {
                 const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
                 if (mv_global ? lb < la : (lb << b_shift) < la) {
                     items = lb;
-                    base = x0;
-                    meta = __ffs((int)(x1 - x0));  // log2 + 1
+                    base = (int64_t)(hd >> 8);
+                    meta = (int)(hd & 0xFFu) + 1;  // log2 + 1
                 }
             }
         }
@@ -518,9 +518,9 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
     const uint32_t* Mp = M;
     int log_mp = log_m;
     if (!useM) {
-        const int64_t x0 = p.hoff[v], x1 = p.hoff[v + 1];
-        Mp = p.htab + x0;
-        log_mp = __ffsll((unsigned long long)(x1 - x0)) - 1;
+        const uint64_t hd = p.hdesc[v];
+        Mp = p.htab + (hd >> 8);
+        log_mp = (int)(hd & 0xFFu);
     }
     if (useM) {
         for (int s = tid; s < (1 << log_m); s += nthr) M[s] = kEmpty;

@@ -45,11 +45,15 @@ struct RoundCounters {
     long long T;                  // labels so far (graph mode)
     long long lcap, hcap;         // label and probe-index buffer capacities (graph mode)
     long long fcap[2];            // new-frontier buffer capacity per parity (graph mode)
+    long long hnext;              // probe index: first free table slot
+    int hovf;                     // probe index: a table did not fit (the index must be rebuilt)
 };
 
 // RoundCounters::fallback: why a graph stopped (1: after the gather, a buffer
-// was too small; kStopBeforeGather: the candidate bound exceeds the frontier buffer).
+// was too small; kStopBeforeGather: the candidate bound exceeds the frontier
+// buffer; kStopIndex: after a complete round, the probe index needs a rebuild).
 constexpr int kStopBeforeGather = 2;
+constexpr int kStopIndex = 3;
 
 // Per-round statistics written on the device (graph mode).
 struct RoundStat {
@@ -75,7 +79,7 @@ struct GpParams {
     int cand_limit;            // max unique candidates per pass (power of two)
     uint32_t* gscratch;        // block tier: per-block buffer of accepted hubs
     int64_t gscratch_words;    // words per block
-    const int64_t* hoff;       // probe index of L: per row a hub-keyed table (empty rows: none)
+    const uint64_t* hdesc;     // probe index of L: per row (table start << 8 | log2 slots), 0 = no table
     const uint32_t* htab;
     const uint32_t* top;       // per vertex: top-hub masks by distance level (see kTopHubs)
     const uint32_t* rbound;    // per receiver: candidate bound min(v, messages)

@@ -320,13 +320,29 @@ __global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const
     }
 }
 
-// One warp per indexed row: the table is built in shared memory (rows whose
-// table has up to `slots` slots) and written out whole, empty slots
-// included; larger tables are cleared and filled in place with atomics.
+// Build the table of the sorted row lent[lb, lb + ll) at htab[hb, hb + 2^lg):
+// in the warp's shared-memory buffer when it has up to `slots` slots (then
+// written out whole, empty slots included), else cleared and filled in place.
+__device__ __forceinline__ void build_table(const uint32_t* lent, int64_t lb, int64_t ll, uint32_t* htab,
+                                            int64_t hb, int lg, uint32_t* buf, int slots, int lane) {
+    const int P = 1 << lg;
+    uint32_t* tab = P <= slots ? buf : htab + hb;
+    for (int sl = lane; sl < P; sl += 32) tab[sl] = kEmpty;
+    __syncwarp();
+    for (int64_t j = lane; j < ll; j += 32) map_insert(tab, lg, lent[lb + j]);
+    __syncwarp();
+    if (P <= slots) {
+        for (int sl = lane; sl < P; sl += 32) htab[hb + sl] = buf[sl];
+        __syncwarp();
+    }
+}
 
+// Full rebuild, one warp per 32 rows: row x's table at hoff[x] (sizes from
+// k_index_size and a scan); hdesc[x] = hoff[x] << 8 | log2 size, or 0.
 __global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t* loff, const uint32_t* lent,
-                                                                  const int64_t* hoff, uint32_t* htab, int64_t n,
-                                                                  int slots, const RoundCounters* ctr) {
+                                                                  const int64_t* hoff, uint32_t* htab,
+                                                                  uint64_t* hdesc, int64_t n, int slots,
+                                                                  const RoundCounters* ctr) {
     extern __shared__ uint32_t ibuf[];
     if (ctr->done) return;
     const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -338,6 +354,7 @@ __global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t*
         if (x < n) {
             hb = hoff[x];
             P = hoff[x + 1] - hb;
+            hdesc[x] = P > 0 ? ((uint64_t)hb << 8) | (uint64_t)(__ffsll((unsigned long long)P) - 1) : 0ull;
         }
         unsigned m = __ballot_sync(kFull, P > 0);
         while (m) {
@@ -346,18 +363,59 @@ __global__ void __launch_bounds__(kIndexWarps * 32) k_index_build(const int64_t*
             const int64_t xk = base + k;
             const int64_t hbk = __shfl_sync(kFull, hb, k);
             const int Pk = (int)__shfl_sync(kFull, P, k);
-            const int lg = __ffs(Pk) - 1;
             const int64_t lb = loff[xk], ll = loff[xk + 1] - lb;
-            uint32_t* tab = Pk <= slots ? buf : htab + hbk;
-            for (int sl = lane; sl < Pk; sl += 32) tab[sl] = kEmpty;
-            __syncwarp();
-            for (int64_t j = lane; j < ll; j += 32) map_insert(tab, lg, lent[lb + j]);
-            __syncwarp();
-            if (Pk <= slots) {
-                for (int sl = lane; sl < Pk; sl += 32) htab[hbk + sl] = buf[sl];
-                __syncwarp();
-            }
+            build_table(lent, lb, ll, htab, hbk, __ffs(Pk) - 1, buf, slots, lane);
         }
+    }
+}
+
+// After a full rebuild: the next free slot of the table pool.
+__global__ void k_index_total(const int64_t* hoff, int64_t n, RoundCounters* ctr) {
+    if (ctr->done) return;
+    ctr->hnext = hoff[n];
+    ctr->hovf = 0;
+}
+
+// Incremental update after a merge, one warp per row that changed (the new
+// active list A): a row whose table still has room (size >= 2 |L(x)|) gets
+// this round's new entries (hubs of the new frontier row, distance d) inserted;
+// a row that outgrew its table, or reached kIndexMinLen entries, gets a new
+// table from the pool (the old one is left unused).  A table that does not fit
+// the pool sets hovf: the caller rebuilds the whole index before its next use.
+__global__ void __launch_bounds__(kIndexWarps * 32) k_index_update(const int64_t* loff, const uint32_t* lent,
+                                                                   const uint64_t* fse_new, const uint32_t* fhub_new,
+                                                                   const int32_t* A, uint32_t* htab, uint64_t* hdesc,
+                                                                   long long hcap, int slots, RoundCounters* ctr) {
+    extern __shared__ uint32_t ibuf[];
+    if (ctr->done) return;
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    uint32_t* buf = ibuf + w * slots;
+    const uint32_t d = ctr->d;
+    const int nA = ctr->nA;
+    const int nwarps = gridDim.x * kIndexWarps;
+    for (int i = blockIdx.x * kIndexWarps + w; i < nA; i += nwarps) {
+        const int32_t x = A[i];
+        const int64_t lb = loff[x], ll = loff[x + 1] - lb;
+        if (ll < kIndexMinLen) continue;
+        const int lgn = ceil_log2_i64(2 * ll);
+        const uint64_t hd = hdesc[x];
+        if (hd != 0 && (int)(hd & 0xFFu) >= lgn) {
+            const uint64_t f = fse_new[x];
+            const uint32_t* row = fhub_new + fstart(f);
+            const int c = (int)fcount(f), lg = (int)(hd & 0xFFu);
+            uint32_t* tab = htab + (hd >> 8);
+            for (int j = lane; j < c; j += 32) map_insert(tab, lg, pack(row[j], d));
+            continue;
+        }
+        long long hb = 0;
+        if (lane == 0) hb = (long long)atomicAdd((unsigned long long*)&ctr->hnext, 1ull << lgn);
+        hb = __shfl_sync(kFull, hb, 0);
+        if (hb + ((long long)1 << lgn) > hcap) {
+            if (lane == 0) ctr->hovf = 1;
+            continue;
+        }
+        build_table(lent, lb, ll, htab, hb, lgn, buf, slots, lane);
+        if (lane == 0) hdesc[x] = ((uint64_t)hb << 8) | (uint64_t)lgn;
     }
 }
 
@@ -576,7 +634,7 @@ __global__ void k_g_check(RoundCounters* ctr, RoundStat* stats) {
         return;
     }
     const long long T = ctr->T + acc;
-    if (T > ctr->lcap || 4 * T > ctr->hcap) {  // the merge or the probe index would not fit
+    if (T > ctr->lcap) {  // the merge would not fit
         ctr->fallback = 1;
         ctr->done = 1;
         return;
@@ -587,6 +645,10 @@ __global__ void k_g_check(RoundCounters* ctr, RoundStat* stats) {
 // End of a completed round: flip the buffer parity, clear the per-round counters.
 __global__ void k_g_finish(RoundCounters* ctr) {
     if (ctr->done) return;
+    if (ctr->hovf) {  // the round is complete; the host rebuilds the probe index and resumes
+        ctr->fallback = kStopIndex;
+        ctr->done = 1;
+    }
     ctr->cur ^= 1;
     ctr->cursor = ctr->accepted = ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = 0;
     ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;

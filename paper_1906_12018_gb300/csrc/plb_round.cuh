@@ -31,7 +31,11 @@ __global__ void k_gp_warp(GpParams p);
 __global__ void k_gp_block(GpParams p);
 __global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const RoundCounters* ctr);
 __global__ void k_index_build(const int64_t* loff, const uint32_t* lent, const int64_t* hoff, uint32_t* htab,
-                              int64_t n, int slots, const RoundCounters* ctr);
+                              uint64_t* hdesc, int64_t n, int slots, const RoundCounters* ctr);
+__global__ void k_index_total(const int64_t* hoff, int64_t n, RoundCounters* ctr);
+__global__ void k_index_update(const int64_t* loff, const uint32_t* lent, const uint64_t* fse_new,
+                               const uint32_t* fhub_new, const int32_t* A, uint32_t* htab, uint64_t* hdesc,
+                               long long hcap, int slots, RoundCounters* ctr);
 __global__ void k_set_round(RoundCounters* ctr, uint32_t d);
 __global__ void k_g_begin(RoundCounters* ctr);
 __global__ void k_g_bound(RoundCounters* ctr, int x);
