@@ -363,6 +363,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chunglu20")
+    ap.add_argument("--batch-hubs", type=int, default=0,
+                    help="label in rank batches of this many hubs (Alg. 4); 0 = one batch (Alg. 3)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -395,7 +397,7 @@ def main():
     col = torch.from_numpy(g.col).to(dev)
     o = torch.from_numpy(order).to(dev)
     stream = torch.cuda.current_stream(dev)
-    opts = plb.default_options()
+    opts = plb.default_options(batch_hubs=args.batch_hubs)
 
     for _ in range(max(args.warmup, 3)):
         lab = plb.build(rp, col, o, opts)
@@ -428,7 +430,7 @@ def main():
     labs = []
 
     # kernel-class timings and counters: one profiled build
-    lab = plb.build(rp, col, o, default_options_profile())
+    lab = plb.build(rp, col, o, plb.default_options(profile=1, batch_hubs=args.batch_hubs))
     st = lab.stats()
     gp_ms = sum(st["ms_gather_prune"])
     gp_bytes = gather_prune_bytes(st, g.n)
@@ -507,7 +509,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "n": g.n, "m": g.m, "labels": n_labels,
                        "rounds": st0["rounds"], "l2": "flushed between steps (256 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "batch_hubs": args.batch_hubs},
             "roofline": {"bound": "hbm", "kernel": "gather+prune (k_round1, k_gp_warp, k_gp_block)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
@@ -536,12 +539,6 @@ def main():
 
         dist.destroy_process_group()
     return 0
-
-
-def default_options_profile():
-    from paper_1906_12018_gb300 import plb
-
-    return plb.default_options(profile=1)
 
 
 if __name__ == "__main__":

@@ -74,13 +74,18 @@ typedef struct {
     int32_t block_label_cap;   /* largest |L(v)| the block tier stages in shared memory (default 2048) */
     int32_t block_cand_cap;    /* unique candidates per hub-range pass of the block tier (default 2048) */
     int32_t block_threads;     /* threads of the block tier, 64..256, rounded down to a multiple of 32 (default 256) */
-    int32_t use_graph;         /* 1: run the round loop as ONE captured CUDA graph with a
-                                  device-side while condition (no per-round host sync);
-                                  buffers get fixed capacities (32 labels per vertex, at
-                                  least 2^20); a round that would exceed them is redone
-                                  host-driven.  Default 0 (plb_build_batch without options: 1) */
+    int32_t use_graph;         /* 1: run the rounds after round 1 as a captured CUDA graph with
+                                  a device-side while condition (no per-round host sync);
+                                  buffers get fixed capacities; a round that may not fit
+                                  stops the graph, finishes host-driven after the buffers
+                                  grow, and the graph resumes.  Ignored with batch_hubs.
+                                  Default 0 (plb_build_batch without options: 1) */
     int32_t profile;           /* 1: time each kernel class with CUDA events */
-    int32_t reserved[8];
+    int32_t batch_hubs;        /* > 0: label in batches of this many hubs by rank (BVC-PLL,
+                                  Alg. 4): the rounds of batch i propagate only the hubs of
+                                  ranks [i*batch_hubs, (i+1)*batch_hubs); same labels.
+                                  Default 0 (one batch: VC-PLL, Alg. 3) */
+    int32_t reserved[7];
 } plb_options;
 
 /* Opaque label set (library-owned device memory; free with plb_labels_free). */

@@ -289,7 +289,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                                                           (int64_t)kByteStage * (bthr / 32)));
     const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);
     // scalars (48) + warp sums (34) + histogram (256) + top-hub masks + prefix per thread + 64-bit row
-    // start per thread + set (also kByteStage per warp of byte-map staging) + map + candidate list (limit + 32 per warp) + byte map
+    // start per thread + set (also kByteStage per warp of byte-map staging) + map + candidate list
+    // (limit + 32 per warp) + byte map
     const size_t b_smem = sizeof(uint32_t) * (48 + 34 + 256 + kTopRow + (size_t)((bthr + 2) & ~1) + 2 * (size_t)bthr +
                                               (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) +
                                               (size_t)(block_cand + bthr) + kByteHubs / 4);
@@ -391,8 +392,12 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     };
 
     int status = PLB_OK;
-    int d = 0;          // last completed round
+    int d = 0;          // last completed round (of the current batch)
     bool finished = false;
+    // hubs of the current batch (Alg. 4): ranks [batch_lo, batch_hi); one batch
+    // of all vertices is Alg. 3
+    const int64_t batch = o.batch_hubs > 0 ? std::min<int64_t>(o.batch_hubs, n) : n;
+    int64_t batch_lo = 0, batch_hi = n;
     std::vector<std::pair<int, cudaEvent_t>> round_ev;  // (round, start event)
     std::vector<char> host_stat(PLB_MAX_ROUNDS, 0);     // rounds whose statistics the host recorded
 
@@ -407,7 +412,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             // new-frontier buffer holds every arc
             k_set_round<<<1, 1, 0, s>>>(ctr, 1u);
             k_round1<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
-                roff, rcol, n, fse[nxt], fhub[nxt], (unsigned long long)fcap[nxt], ctr);
+                roff, rcol, n, (int32_t)batch_lo, (int32_t)batch_hi, fse[nxt], fhub[nxt],
+                (unsigned long long)fcap[nxt], ctr);
             st.launches += 2;
             PLB_CK(cudaGetLastError());
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
@@ -472,12 +478,13 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
         const int64_t acc = (int64_t)hctr->accepted;
         if (d < PLB_MAX_ROUNDS) {
-            st.receivers[d] = (int64_t)hctr->nR + hctr->nO1_base + hctr->nO2_base;
-            st.accepted[d] = acc;
-            st.unique_round[d] = (int64_t)hctr->uniq;
-            st.prefiltered_round[d] = (int64_t)hctr->prefiltered;
-            st.probed_round[d] = (int64_t)hctr->probed;
-            st.messages_round[d] = (int64_t)hctr->msgs;
+            // per distance d (summed over the batches of Alg. 4)
+            st.receivers[d] += (int64_t)hctr->nR + hctr->nO1_base + hctr->nO2_base;
+            st.accepted[d] += acc;
+            st.unique_round[d] += (int64_t)hctr->uniq;
+            st.prefiltered_round[d] += (int64_t)hctr->prefiltered;
+            st.probed_round[d] += (int64_t)hctr->probed;
+            st.messages_round[d] += (int64_t)hctr->msgs;
             host_stat[d] = 1;
             if (tm.on) round_ev.push_back({d, r0});
         }
@@ -536,204 +543,220 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     // continues host-driven), after it when its labels exceed the label buffers
     // (they grow and the round's merge runs here).  The graph is then captured
     // again and resumes with the next round.
-    {  // round 1 is always host-driven (one kernel)
-        const int e = host_round(false);
-        if (e != PLB_OK) return e;
-    }
-    if (o.use_graph && !finished) {
-        RoundStat* dstat = pool.alloc<RoundStat>(PLB_MAX_ROUNDS);
-        PLB_ALLOC_OK();
-        PLB_CK(cudaMemsetAsync(dstat, 0, sizeof(RoundStat) * PLB_MAX_ROUNDS, s));
-        int64_t lc = std::max<int64_t>(std::max<int64_t>(32 * n, T + 1024), 1 << 20);
-        auto grow = [&](uint32_t*& buf, int64_t& cap, int64_t want, int64_t keep) -> bool {
-            if (cap >= want) return true;
-            uint32_t* nb = pool.alloc<uint32_t>(want);
-            if (pool.failed) return false;
-            if (keep > 0 && cudaMemcpyAsync(nb, buf, sizeof(uint32_t) * keep, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                return false;
-            pool.release(buf);
-            buf = nb;
-            cap = want;
-            return true;
-        };
-        for (int attempt = 0; attempt < 8 && !finished; ++attempt) {
-            if (!grow(lent[cur], lcap[cur], lc, T) || !grow(lent[cur ^ 1], lcap[cur ^ 1], lc, 0)) return PLB_ERR_OOM;
-            {
-                const int e = build_index(cur, T);  // packed, with room for the segment's updates
-                if (e != PLB_OK) return e;
-            }
-            PLB_CK(cudaStreamSynchronize(s));
-            hctr->d = (unsigned)d;
-            hctr->cur = cur;
-            hctr->T = T;
-            hctr->lcap = std::min(lcap[0], lcap[1]);
-            hctr->hcap = hcap;
-            hctr->fcap[0] = fcap[0];
-            hctr->fcap[1] = fcap[1];
-            PLB_CK(cudaMemcpyAsync(&ctr->d, &hctr->d, sizeof(unsigned), cudaMemcpyHostToDevice, s));
-            PLB_CK(cudaMemcpyAsync(&ctr->cur, &hctr->cur, sizeof(int), cudaMemcpyHostToDevice, s));
-            PLB_CK(cudaMemcpyAsync(&ctr->T, &hctr->T, 5 * sizeof(long long), cudaMemcpyHostToDevice, s));
-            cudaEvent_t ga = tm.on ? tm.mark() : nullptr;
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            struct GraphGuard {
-                cudaGraph_t* g;
-                cudaGraphExec_t* e;
-                ~GraphGuard() {
-                    if (*e) cudaGraphExecDestroy(*e);
-                    if (*g) cudaGraphDestroy(*g);
-                }
-            } gguard{&graph, &exec};
-            PLB_CK(cudaGraphCreate(&graph, 0));
-            cudaGraphConditionalHandle handle;
-            PLB_CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-            cudaGraphNodeParams cp = {};
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = handle;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t cnode;
-            PLB_CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            // capture on a private stream (capture is not allowed on the legacy
-            // default stream); the graph itself is launched on the caller's stream
-            cudaStream_t user_stream = s, cap_stream = nullptr;
-            PLB_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
-            struct StreamGuard {
-                cudaStream_t st;
-                ~StreamGuard() { cudaStreamDestroy(st); }
-            } sguard{cap_stream};
-            s = cap_stream;
-            skip = &ctr->done;
-            PLB_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            cudaError_t ce = cudaSuccess;
-            const int64_t launches0 = st.launches;
-            for (int r = 0; r < 2 && ce == cudaSuccess; ++r) {
-                const int c = cur ^ r, x = c ^ 1;
-                k_g_begin<<<1, 1, 0, s>>>(ctr);
-                ce = launch_frontier(c, x);
-                if (ce == cudaSuccess) {
-                    k_g_bound<<<1, 1, 0, s>>>(ctr, x);
-                    ce = launch_gp(gp_params(c, x, fcap[x]), nullptr);
-                }
-                if (ce == cudaSuccess) {
-                    k_g_check<<<1, 1, 0, s>>>(ctr, dstat);
-                    ce = launch_merge(c, x);
-                }
-                if (ce == cudaSuccess) ce = update_index(x, T);
-                if (ce == cudaSuccess) {
-                    k_g_finish<<<1, 1, 0, s>>>(ctr);
-                    st.launches += 4;  // loop control
-                    ce = cudaGetLastError();
-                }
-            }
-            k_g_cond<<<1, 1, 0, s>>>(ctr, handle);
-            const cudaError_t ee = cudaStreamEndCapture(s, &body);
-            s = user_stream;
-            skip = nullptr;
-            if (ce != cudaSuccess || ee != cudaSuccess) {
-                (void)cudaGetLastError();
-                set_last_error(ce != cudaSuccess ? ce : ee, __LINE__);
-                return PLB_ERR_CUDA;
-            }
-            const int64_t per_pair = st.launches - launches0 + 1;
-            st.launches = launches0;
-            PLB_CK(cudaGraphInstantiate(&exec, graph, 0));
-            PLB_CK(cudaGraphLaunch(exec, s));
-            PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
-            PLB_CK(cudaStreamSynchronize(s));
-            if (tm.on) tm.span(T_GPW, ga, tm.mark());
-            if (hctr->guard) return PLB_ERR_CUDA;
-            const int dd = (int)hctr->d;  // last round started
-            st.launches += per_pair * ((dd - d + 1) / 2);
-            T = hctr->T;
-            cur = hctr->cur;
-            if (hctr->err) {
-                d = dd;
-                status = hctr->err;
-                finished = true;
-                break;
-            }
-            if (!hctr->fallback) {
-                d = dd;
-                finished = true;
-                break;
-            }
-            st.reruns += 1;
-            PLB_CK(cudaMemsetAsync(&ctr->done, 0, sizeof(int) * 2, s));
-            if (hctr->fallback == kStopIndex) {
-                // round dd is complete (parity flipped, counters reset); its probe
-                // index update did not fit: the next segment starts with a rebuild
-                d = dd;
-                continue;
-            }
-            if (hctr->fallback == kStopBeforeGather) {
-                // round dd's candidate bound exceeds the new-frontier buffer:
-                // the round continues host-driven from its gather
-                d = dd - 1;
-                const int e = host_round(true);
-                if (e != PLB_OK) return e;
-                continue;
-            }
-            if (hctr->fovf) {
-                // the new frontier of round dd overflowed its buffer: restore the
-                // round's start state and redo it host-driven
-                d = dd - 1;
-                hctr->nA = hctr->nA_saved;
-                PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
-                PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
-                PLB_CK(cudaMemcpyAsync(&ctr->nA, &hctr->nA, sizeof(int), cudaMemcpyHostToDevice, s));
-                const int e = host_round(false);
-                if (e != PLB_OK) return e;
-                continue;
-            }
-            // the labels of round dd do not fit the label buffers: its gather is
-            // complete, so grow the merge target and finish the round here
-            const int nxt = cur ^ 1;
-            const int64_t Tn = T + (int64_t)hctr->accepted;
-            lc = std::max<int64_t>(Tn + Tn / 2, lc + lc / 2);
-            if (!grow(lent[nxt], lcap[nxt], lc, 0)) return PLB_ERR_OOM;
-            PLB_CK(launch_merge(cur, nxt));
-            T = Tn;
-            cur = nxt;
-            d = dd;
-            {
-                const int e = build_index(cur, T);
-                if (e != PLB_OK) return e;
-            }
+    int rounds_total = 0;
+    for (batch_lo = 0; batch_lo < n && status == PLB_OK; batch_lo += batch) {
+        batch_hi = std::min<int64_t>(n, batch_lo + batch);
+        if (batch_lo > 0) {
+            // the previous batch ended with an empty round: restart the round count
+            // and the per-round counters; its labels stay (the batches of Alg. 4
+            // only restrict which hubs propagate)
+            d = 0;
+            finished = false;
             PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
             PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
         }
-        // per-round statistics written on the device
-        std::vector<RoundStat> hstat(PLB_MAX_ROUNDS);
-        PLB_CK(cudaMemcpyAsync(hstat.data(), dstat, sizeof(RoundStat) * PLB_MAX_ROUNDS, cudaMemcpyDeviceToHost, s));
-        PLB_CK(cudaStreamSynchronize(s));
-        for (int r = 1; r <= d && r < PLB_MAX_ROUNDS; ++r) {
-            if (host_stat[r]) continue;
-            const RoundStat& x = hstat[r];
-            st.receivers[r] = x.receivers;
-            st.accepted[r] = x.accepted;
-            st.unique_round[r] = x.uniq;
-            st.prefiltered_round[r] = x.pref;
-            st.probed_round[r] = x.probed;
-            st.messages_round[r] = x.msgs;
-            st.arcs_scanned += x.arcs;
-            st.messages += x.msgs;
-            st.unique_candidates += x.uniq;
-            st.staged_entries += x.staged;
-            st.probed_entries += x.probed;
-            st.tier_vertices[0] += x.tier0;
-            st.tier_vertices[1] += x.tier1;
+        {  // round 1 is always host-driven (one kernel)
+            const int e = host_round(false);
+            if (e != PLB_OK) return e;
         }
-        // (after 8 graph segments the remaining rounds run host-driven)
-    }
+        if (o.use_graph && batch == n && !finished) {
+            RoundStat* dstat = pool.alloc<RoundStat>(PLB_MAX_ROUNDS);
+            PLB_ALLOC_OK();
+            PLB_CK(cudaMemsetAsync(dstat, 0, sizeof(RoundStat) * PLB_MAX_ROUNDS, s));
+            int64_t lc = std::max<int64_t>(std::max<int64_t>(32 * n, T + 1024), 1 << 20);
+            auto grow = [&](uint32_t*& buf, int64_t& cap, int64_t want, int64_t keep) -> bool {
+                if (cap >= want) return true;
+                uint32_t* nb = pool.alloc<uint32_t>(want);
+                if (pool.failed) return false;
+                if (keep > 0 &&
+                    cudaMemcpyAsync(nb, buf, sizeof(uint32_t) * keep, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    return false;
+                pool.release(buf);
+                buf = nb;
+                cap = want;
+                return true;
+            };
+            for (int attempt = 0; attempt < 8 && !finished; ++attempt) {
+                if (!grow(lent[cur], lcap[cur], lc, T) || !grow(lent[cur ^ 1], lcap[cur ^ 1], lc, 0))
+                    return PLB_ERR_OOM;
+                {
+                    const int e = build_index(cur, T);  // packed, with room for the segment's updates
+                    if (e != PLB_OK) return e;
+                }
+                PLB_CK(cudaStreamSynchronize(s));
+                hctr->d = (unsigned)d;
+                hctr->cur = cur;
+                hctr->T = T;
+                hctr->lcap = std::min(lcap[0], lcap[1]);
+                hctr->hcap = hcap;
+                hctr->fcap[0] = fcap[0];
+                hctr->fcap[1] = fcap[1];
+                PLB_CK(cudaMemcpyAsync(&ctr->d, &hctr->d, sizeof(unsigned), cudaMemcpyHostToDevice, s));
+                PLB_CK(cudaMemcpyAsync(&ctr->cur, &hctr->cur, sizeof(int), cudaMemcpyHostToDevice, s));
+                PLB_CK(cudaMemcpyAsync(&ctr->T, &hctr->T, 5 * sizeof(long long), cudaMemcpyHostToDevice, s));
+                cudaEvent_t ga = tm.on ? tm.mark() : nullptr;
+                cudaGraph_t graph = nullptr;
+                cudaGraphExec_t exec = nullptr;
+                struct GraphGuard {
+                    cudaGraph_t* g;
+                    cudaGraphExec_t* e;
+                    ~GraphGuard() {
+                        if (*e) cudaGraphExecDestroy(*e);
+                        if (*g) cudaGraphDestroy(*g);
+                    }
+                } gguard{&graph, &exec};
+                PLB_CK(cudaGraphCreate(&graph, 0));
+                cudaGraphConditionalHandle handle;
+                PLB_CK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+                cudaGraphNodeParams cp = {};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = handle;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                cudaGraphNode_t cnode;
+                PLB_CK(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp));
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                // capture on a private stream (capture is not allowed on the legacy
+                // default stream); the graph itself is launched on the caller's stream
+                cudaStream_t user_stream = s, cap_stream = nullptr;
+                PLB_CK(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+                struct StreamGuard {
+                    cudaStream_t st;
+                    ~StreamGuard() { cudaStreamDestroy(st); }
+                } sguard{cap_stream};
+                s = cap_stream;
+                skip = &ctr->done;
+                PLB_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                const int64_t launches0 = st.launches;
+                for (int r = 0; r < 2 && ce == cudaSuccess; ++r) {
+                    const int c = cur ^ r, x = c ^ 1;
+                    k_g_begin<<<1, 1, 0, s>>>(ctr);
+                    ce = launch_frontier(c, x);
+                    if (ce == cudaSuccess) {
+                        k_g_bound<<<1, 1, 0, s>>>(ctr, x);
+                        ce = launch_gp(gp_params(c, x, fcap[x]), nullptr);
+                    }
+                    if (ce == cudaSuccess) {
+                        k_g_check<<<1, 1, 0, s>>>(ctr, dstat);
+                        ce = launch_merge(c, x);
+                    }
+                    if (ce == cudaSuccess) ce = update_index(x, T);
+                    if (ce == cudaSuccess) {
+                        k_g_finish<<<1, 1, 0, s>>>(ctr);
+                        st.launches += 4;  // loop control
+                        ce = cudaGetLastError();
+                    }
+                }
+                k_g_cond<<<1, 1, 0, s>>>(ctr, handle);
+                const cudaError_t ee = cudaStreamEndCapture(s, &body);
+                s = user_stream;
+                skip = nullptr;
+                if (ce != cudaSuccess || ee != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    set_last_error(ce != cudaSuccess ? ce : ee, __LINE__);
+                    return PLB_ERR_CUDA;
+                }
+                const int64_t per_pair = st.launches - launches0 + 1;
+                st.launches = launches0;
+                PLB_CK(cudaGraphInstantiate(&exec, graph, 0));
+                PLB_CK(cudaGraphLaunch(exec, s));
+                PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+                PLB_CK(cudaStreamSynchronize(s));
+                if (tm.on) tm.span(T_GPW, ga, tm.mark());
+                if (hctr->guard) return PLB_ERR_CUDA;
+                const int dd = (int)hctr->d;  // last round started
+                st.launches += per_pair * ((dd - d + 1) / 2);
+                T = hctr->T;
+                cur = hctr->cur;
+                if (hctr->err) {
+                    d = dd;
+                    status = hctr->err;
+                    finished = true;
+                    break;
+                }
+                if (!hctr->fallback) {
+                    d = dd;
+                    finished = true;
+                    break;
+                }
+                st.reruns += 1;
+                PLB_CK(cudaMemsetAsync(&ctr->done, 0, sizeof(int) * 2, s));
+                if (hctr->fallback == kStopIndex) {
+                    // round dd is complete (parity flipped, counters reset); its probe
+                    // index update did not fit: the next segment starts with a rebuild
+                    d = dd;
+                    continue;
+                }
+                if (hctr->fallback == kStopBeforeGather) {
+                    // round dd's candidate bound exceeds the new-frontier buffer:
+                    // the round continues host-driven from its gather
+                    d = dd - 1;
+                    const int e = host_round(true);
+                    if (e != PLB_OK) return e;
+                    continue;
+                }
+                if (hctr->fovf) {
+                    // the new frontier of round dd overflowed its buffer: restore the
+                    // round's start state and redo it host-driven
+                    d = dd - 1;
+                    hctr->nA = hctr->nA_saved;
+                    PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
+                    PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
+                    PLB_CK(cudaMemcpyAsync(&ctr->nA, &hctr->nA, sizeof(int), cudaMemcpyHostToDevice, s));
+                    const int e = host_round(false);
+                    if (e != PLB_OK) return e;
+                    continue;
+                }
+                // the labels of round dd do not fit the label buffers: its gather is
+                // complete, so grow the merge target and finish the round here
+                const int nxt = cur ^ 1;
+                const int64_t Tn = T + (int64_t)hctr->accepted;
+                lc = std::max<int64_t>(Tn + Tn / 2, lc + lc / 2);
+                if (!grow(lent[nxt], lcap[nxt], lc, 0)) return PLB_ERR_OOM;
+                PLB_CK(launch_merge(cur, nxt));
+                T = Tn;
+                cur = nxt;
+                d = dd;
+                {
+                    const int e = build_index(cur, T);
+                    if (e != PLB_OK) return e;
+                }
+                PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
+                PLB_CK(cudaMemsetAsync(&ctr->nO1_base, 0, sizeof(int) * 3, s));
+            }
+            // per-round statistics written on the device
+            std::vector<RoundStat> hstat(PLB_MAX_ROUNDS);
+            PLB_CK(cudaMemcpyAsync(hstat.data(), dstat, sizeof(RoundStat) * PLB_MAX_ROUNDS, cudaMemcpyDeviceToHost, s));
+            PLB_CK(cudaStreamSynchronize(s));
+            for (int r = 1; r <= d && r < PLB_MAX_ROUNDS; ++r) {
+                if (host_stat[r]) continue;
+                const RoundStat& x = hstat[r];
+                st.receivers[r] = x.receivers;
+                st.accepted[r] = x.accepted;
+                st.unique_round[r] = x.uniq;
+                st.prefiltered_round[r] = x.pref;
+                st.probed_round[r] = x.probed;
+                st.messages_round[r] = x.msgs;
+                st.arcs_scanned += x.arcs;
+                st.messages += x.msgs;
+                st.unique_candidates += x.uniq;
+                st.staged_entries += x.staged;
+                st.probed_entries += x.probed;
+                st.tier_vertices[0] += x.tier0;
+                st.tier_vertices[1] += x.tier1;
+            }
+            // (after 8 graph segments the remaining rounds run host-driven)
+        }
 
-    // ---- host-driven rounds (from round d + 1)
-    while (!finished) {
-        const int e = host_round(false);
-        if (e != PLB_OK) return e;
-    }
-    st.rounds = d;
+        // ---- host-driven rounds (from round d + 1)
+        while (!finished) {
+            const int e = host_round(false);
+            if (e != PLB_OK) return e;
+        }
+        rounds_total += d;
+    }  // batches
+    st.rounds = rounds_total;
     st.total_labels = T;
     if (status != PLB_OK) return status;
 
@@ -742,7 +765,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     plb_labels* L = new plb_labels();
     L->n = n;
     L->total = T;
-    L->rounds = d;
+    L->rounds = st.rounds;
     auto fail = [&](int code) {
         if (L->off) cudaFreeAsync(L->off, s);
         if (L->packed) cudaFreeAsync(L->packed, s);
@@ -788,7 +811,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             cudaEvent_t end = i + 1 < round_ev.size() ? round_ev[i + 1].second : f0;
             float ms = 0;
             cudaEventElapsedTime(&ms, round_ev[i].second, end);
-            st.ms_round[round_ev[i].first] = ms;
+            st.ms_round[round_ev[i].first] += ms;
         }
     }
     L->stats = st;

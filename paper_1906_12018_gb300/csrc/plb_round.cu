@@ -222,16 +222,17 @@ __global__ void k_after_collect(RoundCounters* ctr) {
     ctr->nA = 0;
 }
 
-// Round 1 (Alg. 3 with d = 1).  The candidates of v are its neighbours a < v
-// (each sends its only label (a, 0)), they are distinct, and none is pruned:
-// a witness w of (a, 1) at v would need d(w, v) + d(w, a) <= 1 with w in
-// L(v) = {(v, 0)} and in L(a) = {(a, 0)}, impossible for a != v.  So
-// dL_1(v) = {a in N(v) : a < v}: one warp per vertex appends it (unsorted;
-// the merge step sorts the rows), clears the other frontier descriptors and
-// restarts the active list.  Counted like the general round: one message,
-// one unique candidate and one accepted label per such neighbour.
-__global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, uint64_t* fse_new, uint32_t* fhub_new,
-                         unsigned long long fcap, RoundCounters* ctr) {
+// Round 1 (Alg. 3 with d = 1) of the hubs [s, e) (all hubs, or one batch of
+// Alg. 4).  The candidates of v are its neighbours a in [s, e) with a < v
+// (each sends its label (a, 0)), they are distinct, and none is pruned: a
+// witness w of (a, 1) at v would need d(w, v) + d(w, a) <= 1, so w = v or
+// w = a, but (v, .) is not a hub of a (v > a) and (a, .) not yet one of v.
+// So dL_1(v) = N(v) n [s, min(e, v)): one warp per vertex appends it
+// (unsorted; the merge step sorts the rows), clears the other frontier
+// descriptors and restarts the active list.  Counted like the general round:
+// one message, one unique candidate and one accepted label per such neighbour.
+__global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
+                         uint64_t* fse_new, uint32_t* fhub_new, unsigned long long fcap, RoundCounters* ctr) {
     if (ctr->done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->nA_saved = ctr->nA;
@@ -249,7 +250,10 @@ __global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, ui
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t j = j0 + 32 * u + lane;
-                k += (j < ne && rcol[j] < v) ? 1 : 0;
+                if (j < ne) {
+                    const int32_t a = rcol[j];
+                    k += (a >= s && a < e && a < v) ? 1 : 0;
+                }
             }
             c += k;
         }
@@ -272,7 +276,7 @@ __global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, ui
         for (int64_t j0 = nb; j0 < ne; j0 += 32) {
             const int64_t j = j0 + lane;
             const int32_t a = j < ne ? rcol[j] : INT32_MAX;
-            const bool up = a < v;
+            const bool up = a >= s && a < e && a < v;
             const unsigned m = __ballot_sync(kFull, up);
             if (up) fhub_new[start + o + __popc(m & ((1u << lane) - 1u))] = (uint32_t)a;
             o += __popc(m);

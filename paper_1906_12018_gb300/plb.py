@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("profile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("batch_hubs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 

@@ -223,6 +223,17 @@ def test_chunglu20_sampled_queries_match_bfs(chunglu20):
         assert np.array_equal(got[i * 500:(i + 1) * 500], D[pairs[i * 500:(i + 1) * 500, 1]])
 
 
+def test_chunglu20_batched_equals_unbatched(chunglu20):
+    """Alg. 4 with four batches of 2^18 hubs gives the same labels (compared
+    on the device, every entry)."""
+    g, order, lab = chunglu20
+    lab_b = gpu_build(g, order, batch_hubs=1 << 18)
+    assert lab_b.total == lab.total
+    for x, y in zip(lab.device_arrays(), lab_b.device_arrays()):
+        assert torch.equal(x, y)
+    lab_b.free()
+
+
 def test_chunglu20_invariants(chunglu20):
     g, order, lab = chunglu20
     off, hub, dist = host_labels(lab)
@@ -326,3 +337,26 @@ def test_largest_vertex_count():
     pairs = np.array([[n - 1, n - 2], [n - 2, 3], [n - 1, 2], [n - 1, n - 1], [0, n - 2], [1, n - 1]], np.int32)
     assert gpu_query(lab, pairs).tolist() == [3, 2, 2, 0, 2, 2]
     lab.free()
+
+
+def test_batched_labels_equal_unbatched(rmat12):
+    """Alg. 4: hubs propagated in rank batches give the canonical labels of
+    Alg. 3 for any batch size, with the same number of labels per distance."""
+    g, order, ref = rmat12
+    base = gpu_build(g, order).stats()
+    r = base["rounds"]
+    for b in (7, 64, 1000):
+        lab = gpu_build(g, order, batch_hubs=b)
+        assert_labels_equal(lab, ref, f"batch {b}")
+        acc = lab.stats()["accepted"]
+        assert acc[:r] == base["accepted"] and not any(acc[r:]), b
+    lab = gpu_build(g, order, batch_hubs=64, use_graph=1)  # graph mode is off in batches
+    assert_labels_equal(lab, ref, "batch 64 graph")
+
+
+@pytest.mark.parametrize("name,g", tiny_graphs(), ids=lambda x: x if isinstance(x, str) else "")
+def test_tiny_graphs_batch_of_one_hub(name, g):
+    """A batch of one hub is PLL's one root at a time (Sec. 4.2)."""
+    for order in orders_for(g):
+        ref = O.chhl(g.off, g.col, order)
+        assert_labels_equal(gpu_build(g, order, batch_hubs=1), ref, name)
