@@ -35,10 +35,12 @@ __device__ __forceinline__ unsigned top_prefilter(const uint32_t* top, const uin
         for (int i = 1; i <= imax; ++i) {
             const int j = min((int)d - i, kTopLevels);
             const uint4* cj = reinterpret_cast<const uint4*>(th + (j - 1) * kTopWords);
-            const uint4 a = cj[0], b = cj[1];
             const uint32_t* e = ev + (i - 1) * kTopWords;
-            hit |= (a.x & e[0]) | (a.y & e[1]) | (a.z & e[2]) | (a.w & e[3]) | (b.x & e[4]) | (b.y & e[5]) |
-                   (b.z & e[6]) | (b.w & e[7]);
+#pragma unroll
+            for (int q = 0; q < kTopWords / 4; ++q) {
+                const uint4 a = cj[q];
+                hit |= (a.x & e[4 * q]) | (a.y & e[4 * q + 1]) | (a.z & e[4 * q + 2]) | (a.w & e[4 * q + 3]);
+            }
         }
     }
     return __ballot_sync(kFull, hit != 0);

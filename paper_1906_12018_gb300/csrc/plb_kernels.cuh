@@ -91,7 +91,11 @@ struct GpParams {
 // those hubs when E_i(v) & C_{d-i}(h) != 0 for some i, E_i = C_i & ~C_{i-1}:
 // the label test restricted to those hubs and distances (exact: a hit is a
 // real witness).
-constexpr int kTopHubs = 256;
+#ifndef PLB_TOP_HUBS
+#define PLB_TOP_HUBS 256
+#endif
+constexpr int kTopHubs = PLB_TOP_HUBS;  // a multiple of 128 (uint4 loads)
+static_assert(kTopHubs % 128 == 0, "top-hub masks are read as uint4");
 constexpr int kTopWords = kTopHubs / 32;             // words per mask
 constexpr int kTopLevels = 7;                        // distance levels 1..7
 constexpr int kTopRow = kTopLevels * kTopWords;      // words per vertex
