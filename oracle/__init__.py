@@ -13,6 +13,11 @@ Functions (each restates one definition or algorithm of the paper, Jin et al.,
 * ``chhl_row``  Def. 2 for a single vertex (usable on large graphs)
 * ``query``     2-hop distance query (Sec. 2.1)
 * ``bfs``       textbook BFS distances
+* ``pll_directed``  the directed form (Sec. 5.1): (L_in, L_out) by a forward
+                and a backward pruned BFS per root
+* ``chhl_directed`` Def. 2 for directed graphs: L_in(v) from the BFS over
+                in-arcs, L_out(v) over out-arcs (``chhl`` on each CSR)
+* ``query_directed`` d(s->t) from L_out(s) and L_in(t)
 
 Labels come back as ``Labels(off, hub, dist)``: rows indexed by original id,
 hub = rank (uint32), dist uint8, each row sorted by hub rank.
@@ -79,6 +84,10 @@ def _load():
     lib.oracle_query.restype = None
     lib.oracle_bfs.argtypes = [I64, P, P, ctypes.c_int32, P]
     lib.oracle_bfs.restype = None
+    lib.oracle_pll_directed.argtypes = [I64, P, P, P, P, P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.oracle_pll_directed.restype = P
+    lib.oracle_query2.argtypes = [I64, P, P, P, P, P, P, P, P]
+    lib.oracle_query2.restype = None
     _lib = lib
     return lib
 
@@ -194,6 +203,41 @@ def query(labels: Labels, pairs) -> np.ndarray:
     dist = labels.dist if labels.total else np.zeros(1, np.uint8)
     if q:
         _load().oracle_query(q, _p(labels.off), _p(hub), _p(dist), _p(pairs), _p(out))
+    return out[:q]
+
+
+def pll_directed(off_out, col_out, off_in, col_in, order):
+    """Directed PLL (Sec. 5.1): returns (L_in, L_out); rows by original id,
+    hubs as ranks.  off_in/col_in is the transpose of off_out/col_out."""
+    n, off_out, col_out, order = _csr_args(off_out, col_out, order)
+    _, off_in, col_in, _ = _csr_args(off_in, col_in, order)
+    lout = ctypes.c_void_p()
+    h = _load().oracle_pll_directed(n, _p(off_out), _p(col_out), _p(off_in), _p(col_in), _p(order),
+                                    ctypes.byref(lout))
+    if not h:
+        raise OverflowError("label distance above 254 (or out of memory)")
+    return _export(h, n), _export(lout.value, n)
+
+
+def chhl_directed(off_out, col_out, off_in, col_in, order):
+    """Def. 2 for directed graphs: (L_in, L_out).  h is in L_in(v) iff it
+    outranks every vertex of every shortest h->v path: the per-vertex BFS of
+    ``chhl`` over the in-arcs; L_out likewise over the out-arcs."""
+    return chhl(off_in, col_in, order), chhl(off_out, col_out, order)
+
+
+def query_directed(lout: Labels, lin: Labels, pairs) -> np.ndarray:
+    """d(s->t) for int32 pairs [q, 2] from L_out(s) and L_in(t); -1 if none."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    q = int(pairs.shape[0])
+    out = np.empty(max(q, 1), dtype=np.int32)
+
+    def arrs(L):
+        return (L.off, L.hub if L.total else np.zeros(1, np.uint32), L.dist if L.total else np.zeros(1, np.uint8))
+
+    if q:
+        a, b = arrs(lout), arrs(lin)
+        _load().oracle_query2(q, _p(a[0]), _p(a[1]), _p(a[2]), _p(b[0]), _p(b[1]), _p(b[2]), _p(pairs), _p(out))
     return out[:q]
 
 

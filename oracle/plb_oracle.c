@@ -23,6 +23,16 @@
  *                   d(u,h) + d(h,v), by a merge of two hub-sorted lists;
  *                   -1 when no hub is common (different components).
  *   oracle_bfs      textbook BFS distances (-1 unreachable).
+ *   oracle_pll_directed
+ *                   the directed form (Sec. 5.1): per root u in rank order,
+ *                   a forward pruned BFS over out-arcs fills L_in (hub u,
+ *                   d(u->v)) and a backward one over in-arcs fills L_out
+ *                   (hub u, d(v->u)); a candidate is pruned by a hub w with
+ *                   d(u->w) + d(w->v) (resp. d(v->w) + d(w->u)) <= its
+ *                   distance, read from L_out(u) and L_in(v) (resp. L_out(v)
+ *                   and L_in(u)).  Def. 2 for directed graphs is
+ *                   oracle_chhl_row over the in-arcs (L_in) or the out-arcs
+ *                   (L_out); the directed query is oracle_query2.
  *
  * Conventions: vertices are original ids 0..n-1; the order is given as
  * order[r] = id of rank r (rank 0 = highest); label entries store the hub as
@@ -207,6 +217,91 @@ void* oracle_pll(int64_t n, const int64_t* off, const int32_t* col, const int32_
 void* oracle_pll_budget(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order,
                         double budget_s, int64_t* roots_done) {
     return pll_impl(n, off, col, order, budget_s, roots_done);
+}
+
+/* ------------------------------------------------------- directed Alg. 1 */
+/* One pruned BFS from root u (rank r) over the arcs (off, col): v at distance
+ * delta is pruned when a hub w has Tu[w] + d(w, v) <= delta with d(w, v)
+ * read from Lcheck(v); else (r, delta) goes to Ladd(v).  Tu holds the root's
+ * side of the test (d(u->w) or d(w->u)). */
+static int directed_bfs(const int64_t* off, const int32_t* col, const int32_t* rank, int32_t u, int64_t r,
+                        const int32_t* Tu, labels_t* Lcheck, labels_t* Ladd, int32_t* D, int32_t* Q) {
+    int64_t head = 0, tail = 0;
+    int fail = 0;
+    Q[tail++] = u;
+    D[u] = 0;
+    while (head < tail && !fail) {
+        const int32_t v = Q[head++];
+        const int32_t delta = D[v];
+        int pruned = 0;
+        const row_t* Lv = &Lcheck->rows[v];
+        for (int64_t i = 0; i < Lv->len; ++i) {
+            const int32_t tw = Tu[Lv->hub[i]];
+            if (tw != INF_D && tw + (int32_t)Lv->dist[i] <= delta) {
+                pruned = 1;
+                break;
+            }
+        }
+        if (pruned) continue;
+        if (delta > 254 || row_push(&Ladd->rows[v], (uint32_t)r, (uint8_t)delta)) {
+            fail = 1;
+            break;
+        }
+        for (int64_t j = off[v]; j < off[v + 1]; ++j) {
+            const int32_t w = col[j];
+            if (rank[w] > r && D[w] < 0) {               /* small revision */
+                D[w] = delta + 1;
+                Q[tail++] = w;
+            }
+        }
+    }
+    for (int64_t i = 0; i < tail; ++i) D[Q[i]] = -1;
+    return fail;
+}
+
+/* Directed PLL; returns the L_in set and writes the L_out set to *out_lout
+ * (both NULL on failure: allocation or a distance above 254). */
+void* oracle_pll_directed(int64_t n, const int64_t* off_out, const int32_t* col_out, const int64_t* off_in,
+                          const int32_t* col_in, const int32_t* order, void** out_lout) {
+    labels_t* Lin = labels_new(n);
+    labels_t* Lout = labels_new(n);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* Tout = (int32_t*)malloc(sizeof(int32_t) * nn);  /* hub rank -> d(u->hub) */
+    int32_t* Tin = (int32_t*)malloc(sizeof(int32_t) * nn);   /* hub rank -> d(hub->u) */
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* Q = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int fail = 0;
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t i = 0; i < n; ++i) {
+        Tout[i] = Tin[i] = INF_D;
+        D[i] = -1;
+    }
+    for (int64_t r = 0; r < n && !fail; ++r) {
+        const int32_t u = order[r];
+        const row_t* Lo = &Lout->rows[u];
+        const row_t* Li = &Lin->rows[u];
+        const int64_t lo_len = Lo->len, li_len = Li->len;
+        for (int64_t i = 0; i < lo_len; ++i) Tout[Lo->hub[i]] = Lo->dist[i];
+        for (int64_t i = 0; i < li_len; ++i) Tin[Li->hub[i]] = Li->dist[i];
+        /* forward: d(u->w) from L_out(u), d(w->v) from L_in(v); adds to L_in */
+        fail = directed_bfs(off_out, col_out, rank, u, r, Tout, Lin, Lin, D, Q);
+        /* backward: d(w->u) from L_in(u), d(v->w) from L_out(v); adds to L_out */
+        if (!fail) fail = directed_bfs(off_in, col_in, rank, u, r, Tin, Lout, Lout, D, Q);
+        for (int64_t i = 0; i < lo_len; ++i) Tout[Lout->rows[u].hub[i]] = INF_D;
+        for (int64_t i = 0; i < li_len; ++i) Tin[Lin->rows[u].hub[i]] = INF_D;
+    }
+    free(rank); free(Tout); free(Tin); free(D); free(Q);
+    if (fail) {
+        oracle_labels_free(Lin);
+        oracle_labels_free(Lout);
+        *out_lout = NULL;
+        return NULL;
+    }
+    finish_totals(Lin);
+    finish_totals(Lout);
+    *out_lout = Lout;
+    return Lin;
 }
 
 /* ----------------------------------------------------------------- Alg. 3 */
@@ -431,6 +526,31 @@ void oracle_query(int64_t q, const int64_t* off, const uint32_t* hub, const uint
                 ++j;
             } else {
                 const int32_t c = (int32_t)dist[i] + (int32_t)dist[j];
+                if (best < 0 || c < best) best = c;
+                ++i;
+                ++j;
+            }
+        }
+        out[k] = best;
+    }
+}
+
+/* Directed 2-hop query: d(s->t) = min over hubs w of L_out(s) and L_in(t) of
+ * d(s->w) + d(w->t); -1 when none is common. */
+void oracle_query2(int64_t q, const int64_t* off_s, const uint32_t* hub_s, const uint8_t* dist_s,
+                   const int64_t* off_t, const uint32_t* hub_t, const uint8_t* dist_t, const int32_t* pairs,
+                   int32_t* out) {
+    for (int64_t k = 0; k < q; ++k) {
+        const int32_t s = pairs[2 * k], t = pairs[2 * k + 1];
+        int64_t i = off_s[s], ie = off_s[s + 1], j = off_t[t], je = off_t[t + 1];
+        int32_t best = -1;
+        while (i < ie && j < je) {
+            if (hub_s[i] < hub_t[j]) {
+                ++i;
+            } else if (hub_s[i] > hub_t[j]) {
+                ++j;
+            } else {
+                const int32_t c = (int32_t)dist_s[i] + (int32_t)dist_t[j];
                 if (best < 0 || c < best) best = c;
                 ++i;
                 ++j;

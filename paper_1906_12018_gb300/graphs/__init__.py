@@ -188,6 +188,61 @@ def degree_order(g: Graph) -> np.ndarray:
     return order[: g.n]
 
 
+@dataclass
+class DiGraph:
+    """Directed graph: out-arcs (off, col) and their transpose (off_in, col_in);
+    rows sorted, no self-loops, no duplicate arcs."""
+    off: np.ndarray
+    col: np.ndarray
+    off_in: np.ndarray
+    col_in: np.ndarray
+    name: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.off.shape[0] - 1)
+
+    @property
+    def arcs(self) -> int:
+        return int(self.col.shape[0])
+
+
+def _rows(n: int, src: np.ndarray, dst: np.ndarray):
+    key = np.unique(src.astype(np.int64) * n + dst.astype(np.int64))   # sorted by (src, dst), no duplicates
+    s, d = (key // n).astype(np.int64), (key % n).astype(np.int32)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, s + 1, 1)
+    return np.cumsum(off), d
+
+
+def directed_csr(n: int, src, dst, name: str = "") -> DiGraph:
+    """Arcs src[i] -> dst[i]: self-loops and duplicate arcs dropped; the
+    transpose is built too."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    off, col = _rows(n, src, dst)
+    off_in, col_in = _rows(n, dst, src)
+    return DiGraph(off, col, off_in, col_in, name)
+
+
+def rmat_digraph(scale: int, edge_factor: int, seed: int) -> DiGraph:
+    """R-MAT arcs (the same draws as ``rmat_graph``) kept directed: 2^scale
+    vertices, edge_factor * 2^scale arcs before dropping self-loops and
+    duplicates; all vertices kept."""
+    n = 1 << scale
+    src, dst = rmat_edges(scale, edge_factor * n, seed)
+    return directed_csr(n, src, dst, f"rmat-directed{scale}-{edge_factor}-{seed}")
+
+
+def directed_degree_order(g: DiGraph) -> np.ndarray:
+    """order[r] = vertex of rank r: in-degree + out-degree descending, ties by
+    smaller id (the directed reading of Sec. 6.1's degree order)."""
+    deg = np.diff(g.off) + np.diff(g.off_in)
+    return np.lexsort((np.arange(g.n), -deg)).astype(np.int32)
+
+
 def uniform_pairs(n: int, q: int, seed: int) -> np.ndarray:
     """int32[q, 2], s and t i.i.d. uniform on [0, n) (s == t allowed)."""
     lib = _load()
