@@ -155,6 +155,17 @@ int plb_build(const plb_csr* g, const int32_t* vertex_order, const plb_options* 
 int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k,
                     const plb_options* opt, plb_stream stream, plb_labels** outs);
 
+/* Directed graphs (Sec. 5.1): g holds the OUT-arcs (row u lists the w with
+ * an arc u -> w: strictly ascending, in range, no self-loops; the reverse arc
+ * is NOT required).  Builds, in the same vertex-centric rounds, the
+ * canonical in-labels (*l_in: row v holds (h, d(h -> v)) for the hubs h that
+ * outrank every vertex of every shortest h -> v path) and out-labels
+ * (*l_out: (h, d(v -> h)), likewise), each a label set as from plb_build.
+ * Options as plb_build; use_graph and batch_hubs are ignored (host-driven
+ * rounds, one batch).  Errors as plb_build; on error neither set is returned. */
+int plb_build_directed(const plb_csr* g, const int32_t* vertex_order, const plb_options* opt,
+                       plb_stream stream, plb_labels** l_in, plb_labels** l_out);
+
 /* Answer q distance queries (Sec. 2.1): pairs (device, int32[2q],
  * s_i = pairs[2i], t_i = pairs[2i+1], original ids) -> dist_out (device,
  * int32[q]): d(s,t), PLB_UNREACHABLE if no common hub, PLB_BAD_PAIR if an id
@@ -162,6 +173,13 @@ int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k,
  * null pointers or q < 0. */
 int plb_query_batch(const plb_labels* labels, const int32_t* pairs, int64_t q,
                     int32_t* dist_out, plb_stream stream);
+
+/* Directed queries: dist_out[i] = d(s_i -> t_i) = min over hubs h of
+ * l_out(s_i) and l_in(t_i) of d(s_i -> h) + d(h -> t_i), from the two sets of
+ * one plb_build_directed; codes as plb_query_batch.  PLB_ERR_INVALID when
+ * the sets have different vertex counts. */
+int plb_query_directed(const plb_labels* l_out, const plb_labels* l_in, const int32_t* pairs, int64_t q,
+                       int32_t* dist_out, plb_stream stream);
 
 /* Same query over several label sets in one launch: pair i is answered on
  * sets[set_idx[i]] (set_idx device int32[q]); sets is a host array of m label

@@ -9,6 +9,8 @@ namespace plb {
 
 int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
                const plb_options& o, cudaStream_t s, plb_labels** out);
+int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
+                        const plb_options& o, cudaStream_t s, plb_labels** out_in, plb_labels** out_out);
 extern thread_local char g_last_error[256];
 
 namespace {
@@ -157,6 +159,26 @@ int plb_build(const plb_csr* g, const int32_t* vertex_order, const plb_options* 
     (void)cudaGetLastError();
     if (g->n == 0) return empty_labels(out, s);
     return plb::build_core(g->row_ptr, g->col, vertex_order, g->n, g->nnz, o, s, out);
+}
+
+int plb_build_directed(const plb_csr* g, const int32_t* vertex_order, const plb_options* opt, plb_stream stream,
+                       plb_labels** l_in, plb_labels** l_out) {
+    if (!l_in || !l_out) return PLB_ERR_INVALID;
+    const int c = check_csr(g, vertex_order);
+    if (c != PLB_OK) return c;
+    plb_options o;
+    if (opt) o = *opt; else plb_default_options(&o);
+    if (!sane_options(o)) return PLB_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    if (g->n == 0) {
+        const int e = empty_labels(l_in, s);
+        if (e != PLB_OK) return e;
+        const int e2 = empty_labels(l_out, s);
+        if (e2 != PLB_OK) plb_labels_free(*l_in);
+        return e2;
+    }
+    return plb::build_directed_core(g->row_ptr, g->col, vertex_order, g->n, g->nnz, o, s, l_in, l_out);
 }
 
 // One round loop over the disjoint union of parts [0, k) of gs/orders.

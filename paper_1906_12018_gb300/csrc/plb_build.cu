@@ -6,93 +6,9 @@
 #include <cstring>
 #include <vector>
 
-#include "plb_round.cuh"
+#include "plb_host.cuh"
 
 namespace plb {
-
-namespace {
-
-constexpr int kFlatThreads = 256;
-constexpr int kGpWarpThreads = 256;
-
-struct DevPool {
-    cudaStream_t s;
-    std::vector<void*> ptrs;
-    bool failed = false;
-    explicit DevPool(cudaStream_t st) : s(st) {}
-    template <typename T>
-    T* alloc(int64_t count) {
-        void* p = nullptr;
-        const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
-        if (plb::dev_alloc(&p, bytes, s) != cudaSuccess) {
-            (void)cudaGetLastError();
-            failed = true;
-            return nullptr;
-        }
-        ptrs.push_back(p);
-        return static_cast<T*>(p);
-    }
-    void release(void* p) {
-        auto it = std::find(ptrs.begin(), ptrs.end(), p);
-        if (it != ptrs.end()) {
-            cudaFreeAsync(p, s);
-            ptrs.erase(it);
-        }
-    }
-    ~DevPool() {
-        for (void* p : ptrs) cudaFreeAsync(p, s);
-    }
-};
-
-struct Timer {
-    bool on;
-    cudaStream_t s;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[8];
-    std::vector<cudaEvent_t> all;  // every event once (spans may share an end point)
-    explicit Timer(bool enabled, cudaStream_t st) : on(enabled), s(st) {}
-    cudaEvent_t mark() {
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        cudaEventRecord(e, s);
-        all.push_back(e);
-        return e;
-    }
-    void span(int cls, cudaEvent_t a, cudaEvent_t b) { ev[cls].push_back({a, b}); }
-    double total(int cls) {
-        double t = 0;
-        for (auto& p : ev[cls]) {
-            float ms = 0;
-            cudaEventElapsedTime(&ms, p.first, p.second);
-            t += ms;
-        }
-        return t;
-    }
-    ~Timer() {
-        for (cudaEvent_t e : all) cudaEventDestroy(e);
-        (void)cudaGetLastError();
-    }
-};
-enum { T_PREP = 0, T_FRONT = 1, T_GPW = 2, T_GPB = 3, T_GPG = 4, T_MERGE = 5, T_FINAL = 6, T_ALL = 7 };
-
-int grid_for(int64_t items, int threads, int max_blocks) {
-    int64_t b = (items + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > max_blocks) b = max_blocks;
-    return (int)b;
-}
-
-int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 132;
-    }
-    return sms;
-}
-
-}  // namespace
 
 thread_local char g_last_error[256] = "";
 
@@ -100,16 +16,6 @@ void set_last_error(cudaError_t e, int line) {
     snprintf(g_last_error, sizeof(g_last_error), "plb_build.cu:%d: %s (%s)", line, cudaGetErrorString(e),
              cudaGetErrorName(e));
 }
-
-namespace {
-
-int pow2_at_least(int64_t x) {
-    int p = 1;
-    while (p < x) p <<= 1;
-    return p;
-}
-
-}  // namespace
 
 // Core build on a validated-or-trusted CSR.  Returns a status; on success
 // *out holds the labels (rows by original id).
@@ -165,7 +71,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         PLB_CK(cudaMemsetAsync(seen, 0, sizeof(int) * std::max<int64_t>(n, 1), s));
         if (nnz > 0) {
             k_check_cols<<<grid_for((nnz + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(row_ptr, col, n,
-                                                                                               nnz, err);
+                                                                                               nnz, 1, err);
             PLB_CK(cudaGetLastError());
         }
         k_check_order<<<grid_for(n, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(order, n, seen, err);
@@ -335,7 +241,12 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.ctr = ctr;
         p.hdesc = hdesc;
         p.htab = htab;
+        p.loff_h = loff[c];
+        p.lent_h = lent[c];
+        p.hdesc_h = hdesc;
+        p.htab_h = htab;
         p.top = top;
+        p.top_h = top;
         p.gscratch = gacc;
         p.gscratch_words = std::max<int64_t>(n, 1);
         p.rbound = rbound;

@@ -81,12 +81,12 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
     if (valid) {
-        const int64_t hb = p.loff[h];
-        const int la = (int)(p.loff[h + 1] - hb) - 1;
+        const int64_t hb = p.loff_h[h];
+        const int la = (int)(p.loff_h[h + 1] - hb) - 1;
         base = hb;
         items = la;
         if (la >= b_min) {
-            const uint64_t hd = p.hdesc[h];
+            const uint64_t hd = p.hdesc_h[h];
             if (hd) {
                 const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
                 if (mv_global ? lb < la : (lb << b_shift) < la) {
@@ -98,7 +98,7 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
         }
     }
     // candidates with a long check first try the top-hub prefilter
-    const unsigned pf = top_prefilter(p.top, tv, d, h, valid && items >= kPrefilterMinItems);
+    const unsigned pf = top_prefilter(p.top_h, tv, d, h, valid && items >= kPrefilterMinItems);
     if (lane == 0) prefiltered += __popc(pf);
     if ((pf >> lane) & 1u) {
         valid = false;
@@ -122,12 +122,12 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
             const int j = it - exk;
             bool hit = false;
             if (mk == 0) {
-                const uint32_t x = p.lent[bk + j];
+                const uint32_t x = p.lent_h[bk + j];
                 const uint32_t dv = map_find(M, log_m, hub_of(x));
                 hit = dv != kEmpty && dv + dist_of(x) <= d;
             } else {
                 const uint32_t y = lv[j];
-                const uint32_t dh = map_find(p.htab + bk, mk - 1, hub_of(y));
+                const uint32_t dh = map_find(p.htab_h + bk, mk - 1, hub_of(y));
                 hit = dh != kEmpty && dh + dist_of(y) <= d;
             }
             ++probed;

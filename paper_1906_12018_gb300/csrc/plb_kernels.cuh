@@ -82,6 +82,14 @@ struct GpParams {
     const uint64_t* hdesc;     // probe index of L: per row (table start << 8 | log2 slots), 0 = no table
     const uint32_t* htab;
     const uint32_t* top;       // per vertex: top-hub masks by distance level (see kTopHubs)
+    // The candidates' side of the check: rows, probe index and top-hub masks
+    // of the labels h contributes (the same arrays as above for undirected
+    // graphs; for L_in(v) of a directed graph the L_out of h, and vice versa).
+    const int64_t* loff_h;
+    const uint32_t* lent_h;
+    const uint64_t* hdesc_h;
+    const uint32_t* htab_h;
+    const uint32_t* top_h;
     const uint32_t* rbound;    // per receiver: candidate bound min(v, messages)
 };
 

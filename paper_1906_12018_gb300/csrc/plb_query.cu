@@ -23,12 +23,19 @@ struct SetTable {
     SetDesc s[kMaxSets];
 };
 
-__device__ __forceinline__ int32_t answer_pair(const int64_t* off, const uint32_t* ent, int64_t n, int32_t s,
-                                               int32_t t, int lane) {
+// Rows: s in the set (off_s, ent_s), t in (off_t, ent_t); the same set for
+// undirected labels, L_out and L_in for directed ones (d(s -> t)).
+__device__ __forceinline__ int32_t answer_pair2(const int64_t* off_s, const uint32_t* ent_s, const int64_t* off_t,
+                                                const uint32_t* ent_t, int64_t n, int32_t s, int32_t t, int lane) {
     if (s < 0 || t < 0 || (int64_t)s >= n || (int64_t)t >= n) return PLB_BAD_PAIR;
-    int64_t ab = off[s], al = off[s + 1] - ab;
-    int64_t bb = off[t], bl = off[t + 1] - bb;
+    const uint32_t* ent = ent_s;
+    const uint32_t* ent2 = ent_t;
+    int64_t ab = off_s[s], al = off_s[s + 1] - ab;
+    int64_t bb = off_t[t], bl = off_t[t + 1] - bb;
     if (al > bl) {
+        const uint32_t* e = ent;
+        ent = ent2;
+        ent2 = e;
         int64_t x = ab;
         ab = bb;
         bb = x;
@@ -40,15 +47,31 @@ __device__ __forceinline__ int32_t answer_pair(const int64_t* off, const uint32_
     for (int64_t j = lane; j < al; j += 32) {
         const uint32_t x = ent[ab + j];
         const uint32_t key = pack(hub_of(x), 0);
-        const int64_t pos = lower_bound_u32(ent + bb, bl, key);
+        const int64_t pos = lower_bound_u32(ent2 + bb, bl, key);
         if (pos < bl) {
-            const uint32_t y = ent[bb + pos];
+            const uint32_t y = ent2[bb + pos];
             if (hub_of(y) == hub_of(x)) best = min(best, dist_of(x) + dist_of(y));
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
     return best == 0xFFFFFFFFu ? PLB_UNREACHABLE : (int32_t)best;
+}
+
+__device__ __forceinline__ int32_t answer_pair(const int64_t* off, const uint32_t* ent, int64_t n, int32_t s,
+                                               int32_t t, int lane) {
+    return answer_pair2(off, ent, off, ent, n, s, t, lane);
+}
+
+__global__ void __launch_bounds__(kQThreads) k_query2(const int64_t* off_s, const uint32_t* ent_s,
+                                                      const int64_t* off_t, const uint32_t* ent_t, int64_t n,
+                                                      const int32_t* pairs, int64_t q, int32_t* out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < q; i += nw) {
+        const int32_t r = answer_pair2(off_s, ent_s, off_t, ent_t, n, pairs[2 * i], pairs[2 * i + 1], lane);
+        if (lane == 0) out[i] = r;
+    }
 }
 
 __global__ void __launch_bounds__(kQThreads) k_query(const int64_t* off, const uint32_t* ent, int64_t n,
@@ -105,6 +128,16 @@ extern "C" int plb_query_batch(const plb_labels* L, const int32_t* pairs, int64_
     (void)cudaGetLastError();
     plb::k_query<<<plb::query_grid(q), plb::kQThreads, 0, (cudaStream_t)stream>>>(L->off, L->packed, L->n, pairs, q,
                                                                                   dist_out);
+    return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
+}
+
+extern "C" int plb_query_directed(const plb_labels* L_out, const plb_labels* L_in, const int32_t* pairs, int64_t q,
+                                  int32_t* dist_out, plb_stream stream) {
+    if (!L_out || !L_in || L_out->n != L_in->n || q < 0 || (q > 0 && (!pairs || !dist_out))) return PLB_ERR_INVALID;
+    if (q == 0) return PLB_OK;
+    (void)cudaGetLastError();
+    plb::k_query2<<<plb::query_grid(q), plb::kQThreads, 0, (cudaStream_t)stream>>>(
+        L_out->off, L_out->packed, L_in->off, L_in->packed, L_out->n, pairs, q, dist_out);
     return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
 }
 

@@ -32,9 +32,10 @@ __global__ void k_check_rowptr(const int64_t* row_ptr, int64_t n, int64_t nnz, i
     }
 }
 
-// Per arc (u -> c): 0 <= c < n, c != u, rows strictly ascending, and the
-// reverse arc (c -> u) exists (binary search in row c).
-__global__ void k_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int* err) {
+// Per arc (u -> c): 0 <= c < n, c != u, rows strictly ascending, and (when
+// symmetric) the reverse arc (c -> u) exists (binary search in row c).
+__global__ void k_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int symmetric,
+                             int* err) {
     __shared__ int64_t sh_r[2];
     const int64_t ntiles = (nnz + kTileItems - 1) / kTileItems;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -48,7 +49,7 @@ __global__ void k_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t
             const int32_t c = col[p];
             bool bad = c < 0 || (int64_t)c >= n || (int64_t)c == u;
             if (!bad && p > row_ptr[u] && col[p - 1] >= c) bad = true;
-            if (!bad) {
+            if (!bad && symmetric) {
                 const int64_t b = row_ptr[c], e = row_ptr[c + 1];
                 int64_t lo = b, hi = e;
                 while (lo < hi) {
@@ -69,6 +70,33 @@ __global__ void k_check_order(const int32_t* order, int64_t n, int* seen, int* e
             atomicOr(err, 4);
         } else if (atomicAdd(seen + id, 1) != 0) {
             atomicOr(err, 4);
+        }
+    }
+}
+
+// ------------------------------------------------------------ transpose
+// In-degrees of the rank-space arcs (indeg zeroed by the caller).
+__global__ void k_in_degree(const int32_t* rcol, int64_t nnz, int64_t* indeg) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd((unsigned long long*)&indeg[rcol[p]], 1ull);
+}
+
+// rcol_t: the transpose of (roff, rcol) at row offsets roff_t; fill[] counts
+// the entries placed per row (zeroed by the caller; rows come out unsorted).
+__global__ void k_transpose(const int64_t* roff, const int32_t* rcol, int64_t n, int64_t nnz, const int64_t* roff_t,
+                            unsigned long long* fill, int32_t* rcol_t) {
+    __shared__ int64_t sh_r[2];
+    const int64_t ntiles = (nnz + kTileItems - 1) / kTileItems;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kTileItems, p1 = min(nnz, p0 + kTileItems);
+        __syncthreads();
+        if (threadIdx.x == 0) tile_rows(roff, n, p0, p1, &sh_r[0], &sh_r[1]);
+        __syncthreads();
+        const int64_t r0 = sh_r[0], r1 = sh_r[1];
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const int64_t u = row_of(roff, r0, r1, p);
+            const int32_t w = rcol[p];
+            rcol_t[roff_t[w] + (int64_t)atomicAdd(&fill[w], 1ull)] = (int32_t)u;
         }
     }
 }

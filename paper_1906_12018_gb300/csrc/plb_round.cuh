@@ -7,7 +7,11 @@
 namespace plb {
 
 __global__ void k_check_rowptr(const int64_t* row_ptr, int64_t n, int64_t nnz, int* err);
-__global__ void k_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int* err);
+__global__ void k_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int symmetric,
+                             int* err);
+__global__ void k_in_degree(const int32_t* rcol, int64_t nnz, int64_t* indeg);
+__global__ void k_transpose(const int64_t* roff, const int32_t* rcol, int64_t n, int64_t nnz, const int64_t* roff_t,
+                            unsigned long long* fill, int32_t* rcol_t);
 __global__ void k_check_order(const int32_t* order, int64_t n, int* seen, int* err);
 __global__ void k_inverse(const int32_t* order, int32_t* inv, int64_t n);
 __global__ void k_rank_degree(const int64_t* row_ptr, const int32_t* order, int64_t* rdeg, int64_t n);

@@ -162,6 +162,11 @@ def _lib():
     lib.plb_query_batch.restype = I
     lib.plb_query_multi.argtypes = [ctypes.POINTER(P), I64, P, P, I64, P, P]
     lib.plb_query_multi.restype = I
+    lib.plb_build_directed.argtypes = [ctypes.POINTER(CSR), P, ctypes.POINTER(Options), P, ctypes.POINTER(P),
+                                       ctypes.POINTER(P)]
+    lib.plb_build_directed.restype = I
+    lib.plb_query_directed.argtypes = [P, P, P, I64, P, P]
+    lib.plb_query_directed.restype = I
     lib.plb_labels_view.argtypes = [P, ctypes.POINTER(LabelView)]
     lib.plb_labels_view.restype = I
     lib.plb_labels_stats.argtypes = [P, ctypes.POINTER(BuildStats)]
@@ -188,7 +193,8 @@ def _lib():
 
 def exported_symbols() -> list[str]:
     """Names of the entry points declared in include/plb.h."""
-    return ["plb_default_options", "plb_build", "plb_build_batch", "plb_query_batch", "plb_query_multi",
+    return ["plb_default_options", "plb_build", "plb_build_batch", "plb_build_directed", "plb_query_batch",
+            "plb_query_directed", "plb_query_multi",
             "plb_labels_view", "plb_labels_stats", "plb_labels_bytes", "plb_labels_free", "plb_release_cached_memory",
             "plb_degree_order",
             "plb_degree_order_noalloc", "plb_strerror", "plb_last_error", "plb_version"]
@@ -333,6 +339,34 @@ def build_batch(graphs: Sequence, options: Options | None = None, stream=None, *
     _check(_lib().plb_build_batch(csrs, orders, k, ctypes.byref(opt) if opt is not None else None,
                                   _stream(stream), outs), "plb_build_batch")
     return [Labels(outs[i]) for i in range(k)]
+
+
+def build_directed(row_ptr: torch.Tensor, col: torch.Tensor, order: torch.Tensor, options: Options | None = None,
+                   stream=None, **kw) -> tuple[Labels, Labels]:
+    """plb_build_directed: (row_ptr, col) are the OUT-arcs (device int64[n+1],
+    int32[arcs]); returns (L_in, L_out)."""
+    g = _csr(row_ptr, col)
+    _dev(order, torch.int32, "order")
+    if options is None:
+        options = default_options(**kw)
+    hi, ho = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(_lib().plb_build_directed(ctypes.byref(g), order.data_ptr() if order.numel() else None,
+                                     ctypes.byref(options), _stream(stream), ctypes.byref(hi), ctypes.byref(ho)),
+           "plb_build_directed")
+    return Labels(hi.value), Labels(ho.value)
+
+
+def query_directed(l_out: Labels, l_in: Labels, pairs: torch.Tensor, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """d(s -> t) for CUDA int32 pairs [q, 2] from the two sets of build_directed."""
+    pairs = _dev(pairs.reshape(-1), torch.int32, "pairs")
+    q = pairs.numel() // 2
+    if out is None:
+        out = torch.empty(q, dtype=torch.int32, device=pairs.device)
+    _dev(out, torch.int32, "out")
+    _check(_lib().plb_query_directed(l_out.handle, l_in.handle, pairs.data_ptr(), q, out.data_ptr() if q else None,
+                                     _stream(stream)), "plb_query_directed")
+    return out
 
 
 def query_multi(sets: Sequence[Labels], set_idx: torch.Tensor, pairs: torch.Tensor,
