@@ -288,6 +288,66 @@ def run_batch(args):
     return 0
 
 
+def run_directed(args):
+    """Directed labeling (Sec. 5.1): R-MAT arcs kept directed (2^scale vertices,
+    edge factor 16, seed 3), in + out degree order; one step = one
+    plb_build_directed (L_in and L_out) with the arcs resident on the device."""
+    import torch
+
+    from paper_1906_12018_gb300 import graphs as G
+    from paper_1906_12018_gb300 import plb
+
+    dev = torch.device("cuda", 0)
+    g = G.rmat_digraph(args.directed_scale, 16, 3)
+    order = G.directed_degree_order(g)
+    rp = torch.from_numpy(g.off).to(dev)
+    col = torch.from_numpy(g.col).to(dev)
+    o = torch.from_numpy(order).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        for lab in plb.build_directed(rp, col, o):
+            lab.free()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    labs = None
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        labs = plb.build_directed(rp, col, o)
+        ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if k + 1 < args.steps:
+            for lab in labs:
+                lab.free()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    lin, lout = labs
+    st_in, st_out = lin.stats(), lout.stats()
+    pairs = torch.from_numpy(G.uniform_pairs(g.n, 1 << 16, 4)).to(dev)
+    out = torch.empty(1 << 16, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        plb.query_directed(lout, lin, pairs, out)
+    qev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for a, b in qev:
+        flush.zero_()
+        a.record(stream)
+        plb.query_directed(lout, lin, pairs, out)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    qms = statistics.median(a.elapsed_time(b) for a, b in qev)
+    line = {"metric": "labeling arcs/sec (directed)", "value": g.arcs / (ms / 1e3), "unit": "arcs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"rmat-directed{args.directed_scale}-16-3", "n": g.n, "arcs": g.arcs,
+                       "labels_in": lin.total, "labels_out": lout.total, "rounds": [st_in["rounds"], st_out["rounds"]],
+                       "l2": "flushed between steps (256 MB write)"},
+            "queries": {"value": (1 << 16) / (qms / 1e3), "unit": "queries/s", "batch": 1 << 16},
+            "gpu_launches": st_in["launches"] * args.steps}
+    print(json.dumps(line), flush=True)
+    lin.free()
+    lout.free()
+    return 0
+
+
 def run_serve(args):
     """Serving: R-MAT scale-22 labels resident; labeling jobs drawn from the
     small-graph distribution; query requests with Poisson arrivals and
@@ -389,7 +449,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--mode", default="build", choices=["build", "batch", "serve"])
+    ap.add_argument("--mode", default="build", choices=["build", "batch", "serve", "directed"])
+    ap.add_argument("--directed-scale", type=int, default=20)
     ap.add_argument("--batch-graphs", type=int, default=2000)
     ap.add_argument("--serve-resident", default="rmat22")
     ap.add_argument("--serve-seconds", type=float, default=6.0)
@@ -404,6 +465,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "directed":
+        return run_directed(args)
 
     import torch
 
