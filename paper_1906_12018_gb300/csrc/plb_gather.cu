@@ -74,9 +74,8 @@ __device__ __forceinline__ void stage_exact_levels(const uint32_t* top, int32_t 
 // witness.  Returns the lanes whose candidate survives.
 __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, const uint32_t* M, int log_m,
                                                 bool mv_global, int b_min, int b_shift, const uint32_t* lv,
-                                                int64_t lvlen, uint32_t h, bool valid, unsigned* pm_sm,
-                                                unsigned long long& probed, const uint32_t* tv,
-                                                unsigned long long& prefiltered) {
+                                                int64_t lvlen, uint32_t h, bool valid, unsigned long long& probed,
+                                                const uint32_t* tv, unsigned long long& prefiltered) {
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
@@ -105,22 +104,20 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
         items = 0;
     }
     const unsigned vmask = __ballot_sync(kFull, valid);
-    if (lane == 0) *pm_sm = 0;
     const int incl = warp_incl_scan(items, lane);
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - items;
-    __syncwarp();
+    unsigned pm = 0;  // candidates with a witness so far (the same in every lane)
     for (int ib = 0; ib < total; ib += 32) {
-        const unsigned pm = *(volatile unsigned*)pm_sm;
         if ((pm & vmask) == vmask) break;
         const int it = ib + lane;
         const int k = warp_owner(excl, it);
         const int64_t bk = __shfl_sync(kFull, base, k);
         const int exk = __shfl_sync(kFull, excl, k);
         const int mk = __shfl_sync(kFull, meta, k);
+        bool hit = false;
         if (it < total && !((pm >> k) & 1u)) {
             const int j = it - exk;
-            bool hit = false;
             if (mk == 0) {
                 const uint32_t x = p.lent_h[bk + j];
                 const uint32_t dv = map_find(M, log_m, hub_of(x));
@@ -131,12 +128,9 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
                 hit = dh != kEmpty && dh + dist_of(y) <= d;
             }
             ++probed;
-            if (hit) atomicOr(pm_sm, 1u << k);
         }
-        __syncwarp();
+        pm |= __reduce_or_sync(kFull, hit ? 1u << k : 0u);
     }
-    const unsigned pm = *(volatile unsigned*)pm_sm;
-    __syncwarp();
     return vmask & ~pm;
 }
 
@@ -392,7 +386,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
     const int lane = lane_id(), wib = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int S_CAP = 1 << p.log_s, M_CAP = 1 << p.log_m;
-    int* wsc = reinterpret_cast<int*>(sm) + wib * 4;  // [0] unique count [1] overflow [3] pruned mask
+    int* wsc = reinterpret_cast<int*>(sm) + wib * 4;  // [0] unique count [1] overflow
     uint32_t* tvs = sm + 4 * nwarps;                   // per warp: v's exact-distance top-hub masks
     uint32_t* S = tvs + nwarps * kTopRow + wib * (S_CAP + M_CAP);
     uint32_t* M = S + S_CAP;
@@ -458,8 +452,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
             const unsigned okm = check_chunk(p, d, M, log_m, false, kWarpSideBMin, kWarpSideBShift, p.lent + lb, ll, h,
-                                             valid, (unsigned*)&wsc[3],
-                                             c_probed, tv, c_pref);
+                                             valid, c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
@@ -493,7 +486,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
 
 // Block-per-vertex scalars in shared memory (ints)
 enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_HI = 4, SH_TMP = 5, SH_START = 6 /* 2 ints */,
-       SH_PM = 16 /* one word per warp */, SH_WORDS = 48 };
+       SH_WORDS = 48 };
 
 // One block per vertex, any size.  The candidates are processed in passes
 // over hub ranges [lo, hi): each pass gathers the messages of its range into
@@ -605,8 +598,7 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
                 for (int cb = 0; cb < nchk; cb += 32) {
                     const uint32_t h = stage[cb + lane];
                     const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lv,
-                                                     ll, h, true,
-                                                     (unsigned*)&sh[SH_PM + wid], cnt[4], tv, cnt[7]);
+                                                     ll, h, true, cnt[4], tv, cnt[7]);
                     int base = 0;
                     if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
                     base = __shfl_sync(kFull, base, 0);
@@ -636,8 +628,7 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
             // without the map, set candidates may be hubs of v already
             if (!useM && valid && cb + lane < nc_set && map_find(Mp, log_mp, h) != kEmpty) valid = false;
             const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lv, ll, h,
-                                             valid, (unsigned*)&sh[SH_PM + wid],
-                                             cnt[4], tv, cnt[7]);
+                                             valid, cnt[4], tv, cnt[7]);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
             base = __shfl_sync(kFull, base, 0);
