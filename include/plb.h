@@ -127,7 +127,9 @@ typedef struct {
     int64_t probed_entries;         /* L(h) or L(v) entries probed in distance checks */
     int64_t tier_vertices[3];       /* vertex-rounds: [0] round 1 and the warp tier, [1] block tier, [2] 0 */
     /* milliseconds on the device (profile = 1 only; else 0) */
-    /* ms_gather_prune: [0] round 1 and the warp tier, [1] block tier, [2] 0 */
+    /* ms_gather_prune: [0] round 1 and the warp tier, [1] block tier (host-driven rounds run the two
+       tiers concurrently: [1] is then the time the block tier outlasts the warp tier plus the
+       escalated vertices), [2] 0 */
     double ms_total, ms_prepare, ms_frontier, ms_gather_prune[3], ms_merge, ms_finalize;
     int64_t launches;               /* kernels launched by this build */
 } plb_build_stats;

@@ -114,6 +114,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int32_t* A = pool.alloc<int32_t>(n);
     int32_t* R = pool.alloc<int32_t>(n);
     int32_t* O1 = pool.alloc<int32_t>(n);
+    int32_t* O2 = pool.alloc<int32_t>(n);  // warp-tier escalations when the two tiers run concurrently
     uint32_t* rbound = pool.alloc<uint32_t>(n);
     int64_t* aoff = pool.alloc<int64_t>(n + 1);
     PLB_ALLOC_OK();
@@ -263,24 +264,64 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         st.launches += 4 + scan_n;
         return cudaGetLastError();
     };
+    // Host-driven rounds run the two tiers concurrently: the block tier on a
+    // side stream over k_collect's block list while the warp tier runs on the
+    // build's stream and escalates into a second list, taken by one more
+    // block-tier launch after both (the tails of the two kernels overlap).
+    // Captured rounds (graph mode) run them one after the other.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    PLB_CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    PLB_CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    PLB_CK(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    struct SideGuard {
+        cudaStream_t st;
+        cudaEvent_t a, b;
+        ~SideGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            cudaStreamDestroy(st);
+        }
+    } side_guard{side, ev_fork, ev_join};
     auto launch_gp = [&](GpParams p, cudaEvent_t* g1) -> cudaError_t {
-        p.list = R;  // warp tier
-        p.list_n = &ctr->nR;
-        p.esc = O1;
-        p.esc_n = &ctr->nO1;
-        p.log_s = w_log_s;
-        p.log_m = w_log_m;
-        p.cand_limit = warp_cand;
-        k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
+        GpParams w = p, b = p;
+        w.list = R;  // warp tier
+        w.list_n = &ctr->nR;
+        w.log_s = w_log_s;
+        w.log_m = w_log_m;
+        w.cand_limit = warp_cand;
+        b.esc = nullptr;  // block tier (never escalates)
+        b.esc_n = nullptr;
+        b.log_s = b_log_s;
+        b.log_m = b_log_m;
+        b.cand_limit = block_cand;
+        if (skip == nullptr) {
+            w.esc = O2;
+            w.esc_n = &ctr->nO2;
+            b.list = O1;
+            b.list_n = &ctr->nO1;
+            cudaError_t e = cudaEventRecord(ev_fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+            if (e != cudaSuccess) return e;
+            k_gp_block<<<grid_b, bthr, b_smem, side>>>(b);
+            k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(w);
+            if (g1) *g1 = tm.mark();
+            e = cudaEventRecord(ev_join, side);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join, 0);
+            if (e != cudaSuccess) return e;
+            b.list = O2;
+            b.list_n = &ctr->nO2;
+            k_gp_block<<<grid_b, bthr, b_smem, s>>>(b);
+            st.launches += 3;
+            return cudaGetLastError();
+        }
+        w.esc = O1;
+        w.esc_n = &ctr->nO1;
+        k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(w);
         if (g1) *g1 = tm.mark();
-        p.list = O1;  // block tier (never escalates)
-        p.list_n = &ctr->nO1;
-        p.esc = nullptr;
-        p.esc_n = nullptr;
-        p.log_s = b_log_s;
-        p.log_m = b_log_m;
-        p.cand_limit = block_cand;
-        k_gp_block<<<grid_b, bthr, b_smem, s>>>(p);
+        b.list = O1;
+        b.list_n = &ctr->nO1;
+        k_gp_block<<<grid_b, bthr, b_smem, s>>>(b);
         st.launches += 2;
         return cudaGetLastError();
     };
