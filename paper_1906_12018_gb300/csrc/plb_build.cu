@@ -363,10 +363,13 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             // round 1 needs no frontier step and no check (k_round1); the
             // new-frontier buffer holds every arc
             k_set_round<<<1, 1, 0, s>>>(ctr, 1u);
-            k_round1<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
-                roff, rcol, n, (int32_t)batch_lo, (int32_t)batch_hi, fse[nxt], fhub[nxt],
-                (unsigned long long)fcap[nxt], ctr);
-            st.launches += 2;
+            const int g1w = grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap);
+            k_round1_count<<<g1w, kFlatThreads, 0, s>>>(roff, rcol, n, (int32_t)batch_lo, (int32_t)batch_hi, tmp64,
+                                                       ctr);
+            PLB_CK(exclusive_scan_i64(tmp64, tmp64, n, scan_scr, s));
+            k_round1<<<g1w, kFlatThreads, 0, s>>>(roff, rcol, n, (int32_t)batch_lo, (int32_t)batch_hi, tmp64,
+                                                 fse[nxt], fhub[nxt], (unsigned long long)fcap[nxt], ctr);
+            st.launches += 3 + scan_n;
             PLB_CK(cudaGetLastError());
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));

@@ -351,9 +351,12 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
             k_set_round<<<1, 1, 0, s>>>(S.ctr, (uint32_t)d);
             launches += 1;
             if (d == 1) {
-                k_round1<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
-                    S.g_off, S.g_col, n, 0, (int32_t)n, S.fse[x], S.fhub[x], (unsigned long long)S.fcap[x], S.ctr);
-                launches += 1;
+                const int g1w = grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap);
+                k_round1_count<<<g1w, kFlatThreads, 0, s>>>(S.g_off, S.g_col, n, 0, (int32_t)n, tmp64, S.ctr);
+                PLB_CK(exclusive_scan_i64(tmp64, tmp64, n, scan_scr, s));
+                k_round1<<<g1w, kFlatThreads, 0, s>>>(S.g_off, S.g_col, n, 0, (int32_t)n, tmp64, S.fse[x], S.fhub[x],
+                                                     (unsigned long long)S.fcap[x], S.ctr);
+                launches += 2 + scan_n;
                 PLB_CK(cudaGetLastError());
                 continue;
             }

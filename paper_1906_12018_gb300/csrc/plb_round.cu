@@ -259,45 +259,54 @@ __global__ void k_after_collect(RoundCounters* ctr) {
 // (unsorted; the merge step sorts the rows), clears the other frontier
 // descriptors and restarts the active list.  Counted like the general round:
 // one message, one unique candidate and one accepted label per such neighbour.
+// Count pass: cnt[v] = |N(v) n [s, min(e, v))|, one warp per vertex.
+__global__ void k_round1_count(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
+                               int64_t* cnt, const RoundCounters* ctr) {
+    if (ctr->done) return;
+    const int lane = lane_id();
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp0; v < n; v += nwarps) {
+        const int64_t nb = roff[v], ne = roff[v + 1];
+        int c = 0;
+        for (int64_t j0 = nb; j0 < ne; j0 += 128) {  // four independent loads per lane
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t j = j0 + 32 * u + lane;
+                if (j < ne) {
+                    const int32_t a = rcol[j];
+                    c += (a >= s && a < e && a < v) ? 1 : 0;
+                }
+            }
+        }
+        c = warp_sum(c);
+        if (lane == 0) cnt[v] = c;
+    }
+}
+
+// Write pass: row v of the new frontier at start[v] (the exclusive scan of
+// the counts: no shared cursor), start[n] entries in all.
 __global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
-                         uint64_t* fse_new, uint32_t* fhub_new, unsigned long long fcap, RoundCounters* ctr) {
+                         const int64_t* start, uint64_t* fse_new, uint32_t* fhub_new, unsigned long long fcap,
+                         RoundCounters* ctr) {
     if (ctr->done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->nA_saved = ctr->nA;
         ctr->nA = 0;
+        if ((unsigned long long)start[n] > fcap) ctr->fovf = 1;  // cannot happen: the buffer holds every arc
+        else ctr->cursor = (unsigned long long)start[n];
     }
+    if ((unsigned long long)start[n] > fcap) return;
     const int lane = lane_id();
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long c_acc = 0, c_arcs = 0, c_recv = 0;
     for (int64_t v = warp0; v < n; v += nwarps) {
         const int64_t nb = roff[v], ne = roff[v + 1];
-        int c = 0;
-        for (int64_t j0 = nb; j0 < ne; j0 += 128) {  // four independent loads per lane
-            int k = 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t j = j0 + 32 * u + lane;
-                if (j < ne) {
-                    const int32_t a = rcol[j];
-                    k += (a >= s && a < e && a < v) ? 1 : 0;
-                }
-            }
-            c += k;
-        }
-        c = warp_sum(c);
+        const int64_t st = start[v];
+        const int c = (int)(start[v + 1] - st);
         if (c == 0) {
             if (lane == 0) fse_new[v] = 0;
-            continue;
-        }
-        unsigned long long start = 0;
-        if (lane == 0) start = atomicAdd(&ctr->cursor, (unsigned long long)c);
-        start = __shfl_sync(kFull, start, 0);
-        if (start + c > fcap) {  // cannot happen: the buffer holds every arc
-            if (lane == 0) {
-                ctr->fovf = 1;
-                fse_new[v] = 0;
-            }
             continue;
         }
         int o = 0;
@@ -306,16 +315,19 @@ __global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, in
             const int32_t a = j < ne ? rcol[j] : INT32_MAX;
             const bool up = a >= s && a < e && a < v;
             const unsigned m = __ballot_sync(kFull, up);
-            if (up) fhub_new[start + o + __popc(m & ((1u << lane) - 1u))] = (uint32_t)a;
+            if (up) fhub_new[st + o + __popc(m & ((1u << lane) - 1u))] = (uint32_t)a;
             o += __popc(m);
         }
         if (lane == 0) {
-            fse_new[v] = fpack(start, (uint32_t)c);
+            fse_new[v] = fpack((uint64_t)st, (uint32_t)c);
             c_acc += c;
             c_arcs += ne - nb;
             c_recv += 1;
         }
     }
+    c_acc = warp_sum(c_acc);
+    c_arcs = warp_sum(c_arcs);
+    c_recv = warp_sum(c_recv);
     if (lane == 0 && c_recv) {
         atomicAdd(&ctr->accepted, c_acc);
         atomicAdd(&ctr->msgs, c_acc);
