@@ -228,8 +228,11 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
 
     // ------------------------------------------------------------ rounds
     // launch sequences of one round (buffers of parity c -> x = c ^ 1)
-    auto gp_params = [&](int c, int x, int64_t fc) {
+    // placed: the new-frontier buffer holds the bound sum, so the rows go where
+    // the scan of the bounds (aoff, after the frontier step) puts them
+    auto gp_params = [&](int c, int x, int64_t fc, bool placed) {
         GpParams p{};
+        p.ostart = placed ? aoff : nullptr;
         p.roff = roff;
         p.rcol = rcol;
         p.loff = loff[c];
@@ -259,9 +262,14 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         cudaError_t e = exclusive_scan_i64(tmp64, aoff, n, scan_scr, s, skip);
         if (e != cudaSuccess) return e;
         k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(roff, rcol, fse[c], fhub[c], A, aoff, ctr, recv, n);
-        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[c], n, fse[x], R, O1, rbound, ctr, lim);
+        k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[c], n, fse[x], R, O1, rbound, tmp64, ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(ctr);
-        st.launches += 4 + scan_n;
+        // the scan of the candidate bounds places each receiver's new frontier
+        // row (aoff is free again after k_mark); used when the buffer holds
+        // the bound sum, so that no shared cursor is contended
+        e = exclusive_scan_i64(tmp64, aoff, n, scan_scr, s, skip);
+        if (e != cudaSuccess) return e;
+        st.launches += 4 + 2 * scan_n;
         return cudaGetLastError();
     };
     // Host-driven rounds run the two tiers concurrently: the block tier on a
@@ -411,7 +419,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                     st.launches += 1;
                 }
                 cudaEvent_t g0 = tm.on ? tm.mark() : nullptr, g1 = nullptr;
-                PLB_CK(launch_gp(gp_params(cur, nxt, fcap[nxt]), tm.on ? &g1 : nullptr));
+                PLB_CK(launch_gp(gp_params(cur, nxt, fcap[nxt], (int64_t)hctr->bound_sum <= fcap[nxt]),
+                                 tm.on ? &g1 : nullptr));
                 cudaEvent_t g2 = tm.on ? tm.mark() : nullptr;
                 if (tm.on) {
                     tm.span(T_GPW, g0, g1);
@@ -590,7 +599,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                     ce = launch_frontier(c, x);
                     if (ce == cudaSuccess) {
                         k_g_bound<<<1, 1, 0, s>>>(ctr, x);
-                        ce = launch_gp(gp_params(c, x, fcap[x]), nullptr);
+                        ce = launch_gp(gp_params(c, x, fcap[x], true), nullptr);  // k_g_bound checked the bound
                     }
                     if (ce == cudaSuccess) {
                         k_g_check<<<1, 1, 0, s>>>(ctr, dstat);

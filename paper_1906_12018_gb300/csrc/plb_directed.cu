@@ -266,8 +266,8 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
         if (e != cudaSuccess) return e;
         k_mark<<<flat_grid_cap, kFlatThreads, 0, s>>>(S.s_off, S.s_col, S.fse[c], S.fhub[c], S.A, S.aoff, S.ctr,
                                                       S.recv, n);
-        k_collect<<<gflat, kFlatThreads, 0, s>>>(S.recv, S.g_off, S.loff[c], n, S.fse[x], S.R, S.O1, S.rbound, S.ctr,
-                                                 lim);
+        k_collect<<<gflat, kFlatThreads, 0, s>>>(S.recv, S.g_off, S.loff[c], n, S.fse[x], S.R, S.O1, S.rbound, nullptr,
+                                                 S.ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(S.ctr);
         launches += 4 + scan_n;
         return cudaGetLastError();

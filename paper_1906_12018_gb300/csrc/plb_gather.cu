@@ -459,7 +459,9 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
         }
         if (nacc > 0) {
             unsigned long long start = 0;
-            if (lane == 0) start = atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
+            if (lane == 0)
+                start = p.ostart ? (unsigned long long)p.ostart[v]
+                                 : atomicAdd(&p.ctr->cursor, (unsigned long long)nacc);
             start = __shfl_sync(kFull, start, 0);
             if (start + nacc <= p.fcap) {
                 for (int j = lane; j < nacc; j += 32) p.fhub_new[start + j] = S[j];
@@ -642,7 +644,8 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
     }
     if (total_acc > 0) {
         if (tid == 0) {
-            const unsigned long long start = atomicAdd(&p.ctr->cursor, (unsigned long long)total_acc);
+            const unsigned long long start = p.ostart ? (unsigned long long)p.ostart[v]
+                                                      : atomicAdd(&p.ctr->cursor, (unsigned long long)total_acc);
             *(unsigned long long*)(sh + SH_START) = start;
         }
         __syncthreads();

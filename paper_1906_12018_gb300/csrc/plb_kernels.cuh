@@ -91,6 +91,8 @@ struct GpParams {
     const uint32_t* htab_h;
     const uint32_t* top_h;
     const uint32_t* rbound;    // per receiver: candidate bound min(v, messages)
+    const int64_t* ostart;     // per receiver: start of its new frontier row (the scan of the bounds),
+                               // or null (rows reserved with an atomic cursor)
 };
 
 // Witness prefilter: for the kTopHubs highest-ranked hubs, every vertex x

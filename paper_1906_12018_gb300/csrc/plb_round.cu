@@ -202,11 +202,13 @@ __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t*
 
 // Receivers (recv[v] > 0) are routed by the candidate bound min(v, recv[v]),
 // |L(v)| and degree: warp tier (R) or block tier (O1); the bound is kept in
-// rbound[v] (it sizes the warp tier's tables).  Also clears recv and the new
-// frontier descriptors, and sums the bounds.
+// rbound[v] (it sizes the warp tier's tables) and, when obound is given, in
+// obound[v] for every v (0 for non-receivers: its scan places each row of the
+// new frontier).  Also clears recv and the new frontier descriptors, and sums
+// the bounds.
 __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const int64_t* loff, int64_t n,
-                          uint64_t* fse_new, int32_t* R, int32_t* O1, uint32_t* rbound, RoundCounters* ctr,
-                          TierLimits lim) {
+                          uint64_t* fse_new, int32_t* R, int32_t* O1, uint32_t* rbound, int64_t* obound,
+                          RoundCounters* ctr, TierLimits lim) {
     if (ctr->done) return;
     unsigned long long bsum = 0;
     const int lane = lane_id();
@@ -214,6 +216,7 @@ __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const i
         fse_new[v] = 0;
         const unsigned long long c = recv[v];
         int tier = -1;
+        if (obound) obound[v] = c < (unsigned long long)v ? (int64_t)c : v;
         if (c) {
             recv[v] = 0;
             const unsigned long long bound = c < (unsigned long long)v ? c : (unsigned long long)v;

@@ -25,8 +25,8 @@ __global__ void k_mark(const int64_t* roff, const int32_t* rcol, const uint64_t*
                        const int32_t* A, const int64_t* aoff, const RoundCounters* ctr, unsigned long long* recv,
                        int64_t n);
 __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const int64_t* loff, int64_t n,
-                          uint64_t* fse_new, int32_t* R, int32_t* O1, uint32_t* rbound, RoundCounters* ctr,
-                          TierLimits lim);
+                          uint64_t* fse_new, int32_t* R, int32_t* O1, uint32_t* rbound, int64_t* obound,
+                          RoundCounters* ctr, TierLimits lim);
 __global__ void k_after_collect(RoundCounters* ctr);
 __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n);
 __global__ void k_round1_count(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
