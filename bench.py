@@ -518,7 +518,9 @@ def main():
     st = lab.stats()
     gp_ms = sum(st["ms_gather_prune"])
     gp_bytes = gather_prune_bytes(st, g.n)
-    gp_launches = 1 + 2 * (st["rounds"] - 1)  # k_round1, then both tiers in every later round
+    # round 1: k_round1_count and k_round1; every later host-driven round: the
+    # block tier, the warp tier and the block tier over the warp tier's escalations
+    gp_launches = 2 + 3 * (st["rounds"] - 1)
     traffic = recorded_traffic(args.workload)
     peak, peak_kind = measured_peaks()
     achieved = gp_bytes / (gp_ms / 1e3) / 1e9 if gp_ms > 0 else 0.0
@@ -595,7 +597,7 @@ def main():
                        "rounds": st0["rounds"], "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single",
                        "batch_hubs": args.batch_hubs},
-            "roofline": {"bound": "hbm", "kernel": "gather+prune (k_round1, k_gp_warp, k_gp_block)",
+            "roofline": {"bound": "hbm", "kernel": "gather+prune (k_round1_count, k_round1, k_gp_warp, k_gp_block)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if peak else None, "peak_kind": peak_kind,
                          "traffic": traffic[0] if traffic else None,
