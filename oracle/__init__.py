@@ -18,6 +18,11 @@ Functions (each restates one definition or algorithm of the paper, Jin et al.,
 * ``chhl_directed`` Def. 2 for directed graphs: L_in(v) from the BFS over
                 in-arcs, L_out(v) over out-arcs (``chhl`` on each CSR)
 * ``query_directed`` d(s->t) from L_out(s) and L_in(t)
+* ``pll_weighted``  weighted graphs (Sec. 5.1; the Sec. 6.4 baseline): Alg. 1
+                with a pruned Dijkstra search per root
+* ``chhl_weighted``, ``chhl_row_weighted``  Def. 2 for weighted graphs (one
+                Dijkstra per vertex, best rank along the shortest-path DAG)
+* ``dijkstra``  textbook Dijkstra distances
 
 Labels come back as ``Labels(off, hub, dist)``: rows indexed by original id,
 hub = rank (uint32), dist uint8, each row sorted by hub rank.
@@ -88,6 +93,16 @@ def _load():
     lib.oracle_pll_directed.restype = P
     lib.oracle_query2.argtypes = [I64, P, P, P, P, P, P, P, P]
     lib.oracle_query2.restype = None
+    for name in ("oracle_pll_weighted", "oracle_chhl_weighted"):
+        f = getattr(lib, name)
+        f.argtypes = [I64, P, P, P, P]
+        f.restype = P
+    lib.oracle_pll_weighted_budget.argtypes = [I64, P, P, P, P, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]
+    lib.oracle_pll_weighted_budget.restype = P
+    lib.oracle_chhl_row_weighted.argtypes = [I64, P, P, P, P, ctypes.c_int32, P, P, I64]
+    lib.oracle_chhl_row_weighted.restype = I64
+    lib.oracle_dijkstra.argtypes = [I64, P, P, P, ctypes.c_int32, P]
+    lib.oracle_dijkstra.restype = None
     _lib = lib
     return lib
 
@@ -249,4 +264,76 @@ def bfs(off, col, src: int) -> np.ndarray:
     if col.shape[0] == 0:
         col = np.zeros(1, dtype=np.int32)
     _load().oracle_bfs(n, _p(off), _p(col), int(src), _p(dist))
+    return dist[:n]
+
+
+def _weights(wt, nnz: int) -> np.ndarray:
+    wt = np.ascontiguousarray(wt, dtype=np.uint8)
+    if wt.shape[0] != nnz:
+        raise ValueError("one weight per arc")
+    return wt if nnz else np.ones(1, dtype=np.uint8)
+
+
+def pll_weighted(off, col, wt, order) -> Labels:
+    """Alg. 1 on a weighted graph: one pruned Dijkstra search per root in
+    rank order (the PLL baseline of Sec. 6.4).  ``wt`` holds one uint8
+    weight >= 1 per arc, equal in both directions."""
+    nnz = int(np.asarray(col).shape[0])
+    n, off, col, order = _csr_args(off, col, order)
+    wt = _weights(wt, nnz)
+    h = _load().oracle_pll_weighted(n, _p(off), _p(col), _p(wt), _p(order))
+    if not h:
+        raise OverflowError("label distance above 254 (or out of memory)")
+    return _export(h, n)
+
+
+def pll_weighted_budget(off, col, wt, order, seconds: float):
+    """``pll_weighted`` stopped once ``seconds`` have elapsed (between roots):
+    (labels so far, roots done, elapsed seconds)."""
+    import time
+
+    nnz = int(np.asarray(col).shape[0])
+    n, off, col, order = _csr_args(off, col, order)
+    wt = _weights(wt, nnz)
+    done = ctypes.c_int64(0)
+    t0 = time.perf_counter()
+    h = _load().oracle_pll_weighted_budget(n, _p(off), _p(col), _p(wt), _p(order), float(seconds),
+                                           ctypes.byref(done))
+    el = time.perf_counter() - t0
+    if not h:
+        raise OverflowError("label distance above 254 (or out of memory)")
+    return _export(h, n), int(done.value), el
+
+
+def chhl_weighted(off, col, wt, order) -> Labels:
+    """Def. 2 on a weighted graph for every vertex (n Dijkstra runs)."""
+    nnz = int(np.asarray(col).shape[0])
+    n, off, col, order = _csr_args(off, col, order)
+    wt = _weights(wt, nnz)
+    h = _load().oracle_chhl_weighted(n, _p(off), _p(col), _p(wt), _p(order))
+    return _export(h, n)
+
+
+def chhl_row_weighted(off, col, wt, order, v: int):
+    """Def. 2 on a weighted graph for one vertex: (hub ranks, distances)."""
+    nnz = int(np.asarray(col).shape[0])
+    n, off, col, order = _csr_args(off, col, order)
+    wt = _weights(wt, nnz)
+    hub = np.empty(max(n, 1), dtype=np.uint32)
+    dist = np.empty(max(n, 1), dtype=np.uint8)
+    k = _load().oracle_chhl_row_weighted(n, _p(off), _p(col), _p(wt), _p(order), int(v), _p(hub), _p(dist), n)
+    return hub[:k].copy(), dist[:k].copy()
+
+
+def dijkstra(off, col, wt, src: int) -> np.ndarray:
+    """Textbook Dijkstra distances from src (-1 unreachable)."""
+    nnz = int(np.asarray(col).shape[0])
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = int(off.shape[0] - 1)
+    wt = _weights(wt, nnz)
+    if col.shape[0] == 0:
+        col = np.zeros(1, dtype=np.int32)
+    dist = np.empty(max(n, 1), dtype=np.int32)
+    _load().oracle_dijkstra(n, _p(off), _p(col), _p(wt), int(src), _p(dist))
     return dist[:n]

@@ -33,6 +33,14 @@
  *                   and L_in(u)).  Def. 2 for directed graphs is
  *                   oracle_chhl_row over the in-arcs (L_in) or the out-arcs
  *                   (L_out); the directed query is oracle_query2.
+ *   oracle_pll_weighted
+ *                   weighted graphs (Sec. 5.1, Sec. 6.4): Alg. 1 with each
+ *                   pruned BFS replaced by a pruned Dijkstra search (uint8
+ *                   arc weights >= 1, symmetric).
+ *   oracle_chhl_row_weighted, oracle_chhl_weighted
+ *                   Def. 2 for weighted graphs: one Dijkstra from v, best
+ *                   rank carried along the shortest-path DAG in settle order.
+ *   oracle_dijkstra textbook Dijkstra distances (-1 unreachable).
  *
  * Conventions: vertices are original ids 0..n-1; the order is given as
  * order[r] = id of rank r (rank 0 = highest); label entries store the hub as
@@ -576,4 +584,267 @@ void oracle_bfs(int64_t n, const int64_t* off, const int32_t* col, int32_t src, 
             }
     }
     free(Q);
+}
+
+/* ============================================================ weighted graphs
+ * Sec. 5.1 (weighted graphs) and Sec. 6.4: the sequential baseline there is
+ * PLL with its BFS replaced by Dijkstra's algorithm.  Arc weights are uint8,
+ * per arc (wt[j] belongs to col[j]), positive, the same in both directions. */
+
+/* Binary min-heap of keys dist << 32 | vertex (lazy deletion: an entry whose
+ * distance is above the vertex's current tentative distance is skipped). */
+typedef struct {
+    int64_t* key;
+    int64_t len;
+} heap_t;
+
+static void heap_push(heap_t* h, int64_t k) {
+    int64_t i = h->len++;
+    while (i > 0) {
+        const int64_t p = (i - 1) / 2;
+        if (h->key[p] <= k) break;
+        h->key[i] = h->key[p];
+        i = p;
+    }
+    h->key[i] = k;
+}
+
+static int64_t heap_pop(heap_t* h) {
+    const int64_t top = h->key[0];
+    const int64_t last = h->key[--h->len];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= h->len) break;
+        if (c + 1 < h->len && h->key[c + 1] < h->key[c]) ++c;
+        if (h->key[c] >= last) break;
+        h->key[i] = h->key[c];
+        i = c;
+    }
+    if (h->len > 0) h->key[i] = last;
+    return top;
+}
+
+#define HKEY(d, v) (((int64_t)(d) << 32) | (int64_t)(uint32_t)(v))
+#define HDIST(k) ((int32_t)((k) >> 32))
+#define HVERT(k) ((int32_t)((k) & 0xffffffff))
+
+/* PLL with pruned Dijkstra searches (Alg. 1 with Dijkstra in place of BFS):
+ * roots in rank order; a settled vertex v at distance delta is pruned when a
+ * hub w of L(v) has d(u,w) + d(w,v) <= delta (read from L(u), L(v)); else
+ * (u, delta) is appended to L(v) and v relaxes its arcs to vertices u
+ * outranks.  NULL on allocation failure or a distance above 254. */
+static void* pll_weighted_impl(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt,
+                               const int32_t* order, double budget_s, int64_t* roots_done) {
+    const double t_start = now_s();
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const int64_t nnz = off[n];
+    labels_t* L = labels_new(n);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* T = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* D = (int32_t*)malloc(sizeof(int32_t) * nn);   /* tentative distance, -1 untouched */
+    int32_t* touched = (int32_t*)malloc(sizeof(int32_t) * nn);
+    heap_t hp = {(int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz + 2)), 0};
+    int fail = 0;
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t i = 0; i < n; ++i) {
+        T[i] = INF_D;
+        D[i] = -1;
+    }
+    int64_t r = 0;
+    for (r = 0; r < n && !fail; ++r) {
+        if (budget_s > 0 && r > 0 && now_s() - t_start > budget_s) break;
+        const int32_t u = order[r];
+        const row_t* Lu = &L->rows[u];
+        const int64_t lu_len = Lu->len;
+        for (int64_t i = 0; i < lu_len; ++i) T[Lu->hub[i]] = Lu->dist[i];
+        int64_t nt = 0;
+        hp.len = 0;
+        D[u] = 0;
+        touched[nt++] = u;
+        heap_push(&hp, HKEY(0, u));
+        while (hp.len > 0) {
+            const int64_t k = heap_pop(&hp);
+            const int32_t v = HVERT(k), delta = HDIST(k);
+            if (delta != D[v]) continue;                 /* stale entry */
+            int pruned = 0;
+            const row_t* Lv = &L->rows[v];
+            for (int64_t i = 0; i < Lv->len; ++i) {
+                const int32_t tw = T[Lv->hub[i]];
+                if (tw != INF_D && tw + (int32_t)Lv->dist[i] <= delta) {
+                    pruned = 1;
+                    break;
+                }
+            }
+            if (pruned) continue;
+            if (delta > 254) {
+                fail = 1;
+                break;
+            }
+            if (row_push(&L->rows[v], (uint32_t)r, (uint8_t)delta)) {
+                fail = 1;
+                break;
+            }
+            for (int64_t j = off[v]; j < off[v + 1]; ++j) {
+                const int32_t x = col[j];
+                if (rank[x] <= r) continue;                /* small revision */
+                const int32_t nd = delta + (int32_t)wt[j];
+                if (D[x] < 0 || nd < D[x]) {
+                    if (D[x] < 0) touched[nt++] = x;
+                    D[x] = nd;
+                    heap_push(&hp, HKEY(nd, x));
+                }
+            }
+        }
+        for (int64_t i = 0; i < nt; ++i) D[touched[i]] = -1;
+        for (int64_t i = 0; i < lu_len; ++i) T[L->rows[u].hub[i]] = INF_D;
+    }
+    free(rank);
+    free(T);
+    free(D);
+    free(touched);
+    free(hp.key);
+    if (roots_done) *roots_done = r;
+    if (fail) {
+        oracle_labels_free(L);
+        return NULL;
+    }
+    finish_totals(L);
+    return L;
+}
+
+void* oracle_pll_weighted(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt,
+                          const int32_t* order) {
+    return pll_weighted_impl(n, off, col, wt, order, 0.0, NULL);
+}
+
+void* oracle_pll_weighted_budget(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt,
+                                 const int32_t* order, double budget_s, int64_t* roots_done) {
+    return pll_weighted_impl(n, off, col, wt, order, budget_s, roots_done);
+}
+
+/* Dijkstra from src over every vertex: dist (-1 unreachable) and the settle
+ * order (non-decreasing distance); returns the number settled. */
+static int64_t dijkstra_impl(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt, int32_t src,
+                             int32_t* dist, char* done, int32_t* settled, heap_t* hp) {
+    for (int64_t i = 0; i < n; ++i) {
+        dist[i] = -1;
+        done[i] = 0;
+    }
+    int64_t ns = 0;
+    hp->len = 0;
+    dist[src] = 0;
+    heap_push(hp, HKEY(0, src));
+    while (hp->len > 0) {
+        const int64_t k = heap_pop(hp);
+        const int32_t v = HVERT(k), dv = HDIST(k);
+        if (done[v] || dv != dist[v]) continue;
+        done[v] = 1;
+        settled[ns++] = v;
+        for (int64_t j = off[v]; j < off[v + 1]; ++j) {
+            const int32_t x = col[j];
+            const int32_t nd = dv + (int32_t)wt[j];
+            if (!done[x] && (dist[x] < 0 || nd < dist[x])) {
+                dist[x] = nd;
+                heap_push(hp, HKEY(nd, x));
+            }
+        }
+    }
+    return ns;
+}
+
+void oracle_dijkstra(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt, int32_t src,
+                     int32_t* dist) {
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    char* done = (char*)malloc(nn);
+    int32_t* settled = (int32_t*)malloc(sizeof(int32_t) * nn);
+    heap_t hp = {(int64_t*)malloc(sizeof(int64_t) * (size_t)(off[n] + 2)), 0};
+    dijkstra_impl(n, off, col, wt, src, dist, done, settled, &hp);
+    free(done);
+    free(settled);
+    free(hp.key);
+}
+
+/* Def. 2 for one vertex v of a weighted graph: after Dijkstra from v, the
+ * vertices are taken in settle order and best[x] = min(rank(x), best[p] over
+ * the predecessors p of x on shortest paths, d(v,p) + w(p,x) = d(v,x)); with
+ * positive weights every such p settles before x, so best[x] is the highest
+ * rank on all shortest v-x paths and x is a hub of v iff best[x] = rank(x). */
+static int64_t chhl_row_weighted_impl(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt,
+                                      const int32_t* rank, int32_t v, int32_t* dist, int32_t* best, char* done,
+                                      int32_t* settled, heap_t* hp, uint32_t* out_hub, uint8_t* out_dist,
+                                      int64_t cap) {
+    const int64_t ns = dijkstra_impl(n, off, col, wt, v, dist, done, settled, hp);
+    int64_t k = 0;
+    for (int64_t i = 0; i < ns; ++i) {
+        const int32_t x = settled[i];
+        int32_t b = rank[x];
+        for (int64_t j = off[x]; j < off[x + 1]; ++j) {
+            const int32_t p = col[j];
+            if (dist[p] >= 0 && dist[p] + (int32_t)wt[j] == dist[x] && best[p] < b) b = best[p];
+        }
+        best[x] = b;
+        if (b == rank[x]) {
+            if (k < cap) {
+                out_hub[k] = (uint32_t)rank[x];
+                out_dist[k] = (uint8_t)(dist[x] > 255 ? 255 : dist[x]);
+            }
+            ++k;
+        }
+    }
+    if (k > cap) return -1;
+    for (int64_t i = 1; i < k; ++i) {                    /* sort by hub rank */
+        uint32_t h = out_hub[i];
+        uint8_t dd = out_dist[i];
+        int64_t p = i;
+        while (p > 0 && out_hub[p - 1] > h) {
+            out_hub[p] = out_hub[p - 1];
+            out_dist[p] = out_dist[p - 1];
+            --p;
+        }
+        out_hub[p] = h;
+        out_dist[p] = dd;
+    }
+    return k;
+}
+
+int64_t oracle_chhl_row_weighted(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt,
+                                 const int32_t* order, int32_t v, uint32_t* out_hub, uint8_t* out_dist,
+                                 int64_t cap) {
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* best = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* settled = (int32_t*)malloc(sizeof(int32_t) * nn);
+    char* done = (char*)malloc(nn);
+    heap_t hp = {(int64_t*)malloc(sizeof(int64_t) * (size_t)(off[n] + 2)), 0};
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    const int64_t k = chhl_row_weighted_impl(n, off, col, wt, rank, v, dist, best, done, settled, &hp, out_hub,
+                                             out_dist, cap);
+    free(rank); free(dist); free(best); free(settled); free(done); free(hp.key);
+    return k;
+}
+
+/* Def. 2 for every vertex of a weighted graph (n Dijkstra runs). */
+void* oracle_chhl_weighted(int64_t n, const int64_t* off, const int32_t* col, const uint8_t* wt,
+                           const int32_t* order) {
+    labels_t* L = labels_new(n);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* best = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* settled = (int32_t*)malloc(sizeof(int32_t) * nn);
+    char* done = (char*)malloc(nn);
+    uint32_t* hh = (uint32_t*)malloc(sizeof(uint32_t) * nn);
+    uint8_t* dd = (uint8_t*)malloc(nn);
+    heap_t hp = {(int64_t*)malloc(sizeof(int64_t) * (size_t)(off[n] + 2)), 0};
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t k = chhl_row_weighted_impl(n, off, col, wt, rank, (int32_t)v, dist, best, done, settled, &hp,
+                                                 hh, dd, n);
+        for (int64_t i = 0; i < k; ++i) row_push(&L->rows[v], hh[i], dd[i]);
+    }
+    free(rank); free(dist); free(best); free(settled); free(done); free(hh); free(dd); free(hp.key);
+    finish_totals(L);
+    return L;
 }

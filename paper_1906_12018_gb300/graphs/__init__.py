@@ -11,6 +11,7 @@ real datasets, which are not available here):
 * ``chung_lu_graph`` Chung-Lu, weights (i+1)^(-1/(gamma-1)), cleaned
 * ``degree_order``   rank -> id, degree descending, ties by smaller id (Sec. 6.1)
 * ``uniform_pairs``  i.i.d. uniform query pairs
+* ``edge_weights``   seeded uniform integer weights per undirected edge (both arcs alike)
 * ``workload``       the named labeling workloads used by tests and the benchmark
 """
 from __future__ import annotations
@@ -250,6 +251,31 @@ def uniform_pairs(n: int, q: int, seed: int) -> np.ndarray:
     if q > 0:
         lib.gen_uniform_pairs(n, q, seed, _p(pairs))
     return pairs[: 2 * q].reshape(q, 2)
+
+
+def _splitmix64(z: np.ndarray) -> np.ndarray:
+    """SplitMix64 output function (Steele, Lea, Flood 2014) on uint64 arrays."""
+    with np.errstate(over="ignore"):
+        z = z + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def edge_weights(g: Graph, lo: int, hi: int, seed: int) -> np.ndarray:
+    """uint8 weight per arc of g, uniform on [lo, hi] per undirected edge:
+    the arcs u -> v and v -> u hash the same key (min, max, seed), so both
+    directions carry one weight (the paper's weighted inputs draw 1..7
+    uniformly per edge, Sec. 6.1)."""
+    if not 1 <= lo <= hi <= 255:
+        raise ValueError("weights must lie in [1, 255]")
+    src = np.repeat(np.arange(g.n, dtype=np.uint64), np.diff(g.off).astype(np.int64))
+    dst = g.col.astype(np.uint64)
+    a, b = np.minimum(src, dst), np.maximum(src, dst)
+    with np.errstate(over="ignore"):
+        key = (a << np.uint64(32)) ^ b ^ (np.uint64(seed) * np.uint64(0xD1B54A32D192ED03))
+    h = _splitmix64(key)
+    return (np.uint64(lo) + h % np.uint64(hi - lo + 1)).astype(np.uint8)
 
 
 def uniform_int(seed: int, stream: int, i: int, lo: int, hi: int) -> int:
