@@ -168,6 +168,26 @@ int plb_build_batch(const plb_csr* gs, const int32_t* const* orders, int64_t k,
 int plb_build_directed(const plb_csr* g, const int32_t* vertex_order, const plb_options* opt,
                        plb_stream stream, plb_labels** l_in, plb_labels** l_out);
 
+/* Weighted graphs (Sec. 5.1): g as for plb_build (symmetric CSR, device);
+ * weight (device, uint8[nnz]) is the weight of arc j (the arc to col[j]),
+ * at least 1 and equal in both directions.  Builds the canonical labels of
+ * Def. 2 over weighted shortest paths: (h, d(h,v)) is in L(v) iff h outranks
+ * every vertex of every shortest h-v path; the label set has the layout of
+ * plb_build's (distances are weighted, at most PLB_MAX_DIST) and is queried
+ * with plb_query_batch.  Rounds follow the distance: round d accepts the
+ * labels at distance d from the candidates that the frontiers of rounds
+ * d - w send over arcs of weight w, checked against the labels of distance
+ * below d (the snapshot test of Alg. 3), so the result is canonical without
+ * the end-of-batch recheck of Sec. 5.1.  Device memory grows with the
+ * largest weight (one frontier descriptor per vertex and round of the last
+ * max-weight rounds).  Options as plb_build; use_graph and batch_hubs are
+ * ignored (host-driven rounds, one batch).  Errors as plb_build, and
+ * PLB_ERR_INVALID for a null weight array with arcs or a zero weight (always
+ * checked) or, with validate, a weight that differs from its reverse arc's;
+ * PLB_ERR_TOO_LARGE when (largest weight + 1) * n + 1 >= 2^31. */
+int plb_build_weighted(const plb_csr* g, const uint8_t* weight, const int32_t* vertex_order,
+                       const plb_options* opt, plb_stream stream, plb_labels** out);
+
 /* Answer q distance queries (Sec. 2.1): pairs (device, int32[2q],
  * s_i = pairs[2i], t_i = pairs[2i+1], original ids) -> dist_out (device,
  * int32[q]): d(s,t), PLB_UNREACHABLE if no common hub, PLB_BAD_PAIR if an id

@@ -11,6 +11,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                const plb_options& o, cudaStream_t s, plb_labels** out);
 int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
                         const plb_options& o, cudaStream_t s, plb_labels** out_in, plb_labels** out_out);
+int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_t* wt, const int32_t* order,
+                        int64_t n, int64_t nnz, const plb_options& o, cudaStream_t s, plb_labels** out);
 extern thread_local char g_last_error[256];
 
 namespace {
@@ -179,6 +181,21 @@ int plb_build_directed(const plb_csr* g, const int32_t* vertex_order, const plb_
         return e2;
     }
     return plb::build_directed_core(g->row_ptr, g->col, vertex_order, g->n, g->nnz, o, s, l_in, l_out);
+}
+
+int plb_build_weighted(const plb_csr* g, const uint8_t* weight, const int32_t* vertex_order, const plb_options* opt,
+                       plb_stream stream, plb_labels** out) {
+    if (!out) return PLB_ERR_INVALID;
+    const int c = check_csr(g, vertex_order);
+    if (c != PLB_OK) return c;
+    if (g->nnz > 0 && !weight) return PLB_ERR_INVALID;
+    plb_options o;
+    if (opt) o = *opt; else plb_default_options(&o);
+    if (!sane_options(o)) return PLB_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    if (g->n == 0) return empty_labels(out, s);
+    return plb::build_weighted_core(g->row_ptr, g->col, weight, vertex_order, g->n, g->nnz, o, s, out);
 }
 
 // One round loop over the disjoint union of parts [0, k) of gs/orders.

@@ -167,6 +167,8 @@ def _lib():
     lib.plb_build_directed.restype = I
     lib.plb_query_directed.argtypes = [P, P, P, I64, P, P]
     lib.plb_query_directed.restype = I
+    lib.plb_build_weighted.argtypes = [ctypes.POINTER(CSR), P, P, ctypes.POINTER(Options), P, ctypes.POINTER(P)]
+    lib.plb_build_weighted.restype = I
     lib.plb_labels_view.argtypes = [P, ctypes.POINTER(LabelView)]
     lib.plb_labels_view.restype = I
     lib.plb_labels_stats.argtypes = [P, ctypes.POINTER(BuildStats)]
@@ -193,7 +195,8 @@ def _lib():
 
 def exported_symbols() -> list[str]:
     """Names of the entry points declared in include/plb.h."""
-    return ["plb_default_options", "plb_build", "plb_build_batch", "plb_build_directed", "plb_query_batch",
+    return ["plb_default_options", "plb_build", "plb_build_batch", "plb_build_directed", "plb_build_weighted",
+            "plb_query_batch",
             "plb_query_directed", "plb_query_multi",
             "plb_labels_view", "plb_labels_stats", "plb_labels_bytes", "plb_labels_free", "plb_release_cached_memory",
             "plb_degree_order",
@@ -354,6 +357,25 @@ def build_directed(row_ptr: torch.Tensor, col: torch.Tensor, order: torch.Tensor
                                      ctypes.byref(options), _stream(stream), ctypes.byref(hi), ctypes.byref(ho)),
            "plb_build_directed")
     return Labels(hi.value), Labels(ho.value)
+
+
+def build_weighted(row_ptr: torch.Tensor, col: torch.Tensor, weight: torch.Tensor, order: torch.Tensor,
+                   options: Options | None = None, stream=None, **kw) -> Labels:
+    """plb_build_weighted: symmetric CSR (device int64[n+1], int32[arcs]) with
+    one uint8 weight >= 1 per arc (device, equal in both directions);
+    canonical labels over weighted shortest paths, queried with ``query``."""
+    g = _csr(row_ptr, col)
+    _dev(weight, torch.uint8, "weight")
+    _dev(order, torch.int32, "order")
+    if weight.numel() != g.nnz:
+        raise ValueError("one weight per arc")
+    if options is None:
+        options = default_options(**kw)
+    h = ctypes.c_void_p()
+    _check(_lib().plb_build_weighted(ctypes.byref(g), weight.data_ptr() if weight.numel() else None,
+                                     order.data_ptr() if order.numel() else None, ctypes.byref(options),
+                                     _stream(stream), ctypes.byref(h)), "plb_build_weighted")
+    return Labels(h.value)
 
 
 def query_directed(l_out: Labels, l_in: Labels, pairs: torch.Tensor, out: torch.Tensor | None = None,
