@@ -56,60 +56,100 @@ __global__ void k_weight_range(const uint8_t* wt, int64_t nnz, int* mm) {
     }
 }
 
+// Flat kernels over the arcs: tiles of kWTile consecutive arcs, the tile's
+// first and last row found once, each arc's row by binary search between
+// them (rows of any length are spread evenly over the threads).
+constexpr int kWTile = 2048;
+
+__device__ __forceinline__ void tile_bounds(const int64_t* off, int64_t n, int64_t p0, int64_t p1, int64_t* sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sh[0] = row_of(off, 0, n - 1, p0);
+        sh[1] = row_of(off, 0, n - 1, p1 - 1);
+    }
+    __syncthreads();
+}
+
 // Per arc (u -> c) of a validated symmetric CSR: the reverse arc (c -> u),
-// found by binary search in row c, has the same weight.  One warp per row.
+// found by binary search in row c, has the same weight.
 __global__ void k_check_weights(const int64_t* row_ptr, const int32_t* col, const uint8_t* wt, int64_t n,
-                                int* err) {
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
-        bool bad = false;
-        for (int64_t p = row_ptr[u] + wlane(); p < row_ptr[u + 1]; p += 32) {
+                                int64_t nnz, int* err) {
+    __shared__ int64_t sh[2];
+    const int64_t ntiles = (nnz + kWTile - 1) / kWTile;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kWTile, p1 = min(nnz, p0 + kWTile);
+        tile_bounds(row_ptr, n, p0, p1, sh);
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const int64_t u = row_of(row_ptr, sh[0], sh[1], p);
             const int32_t c = col[p];
             int64_t lo = row_ptr[c], hi = row_ptr[c + 1];
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
                 if ((int64_t)col[mid] < u) lo = mid + 1; else hi = mid;
             }
-            if (lo >= row_ptr[c + 1] || (int64_t)col[lo] != u || wt[lo] != wt[p]) bad = true;
+            if (lo >= row_ptr[c + 1] || (int64_t)col[lo] != u || wt[lo] != wt[p]) atomicOr(err, 1);
         }
-        if (__any_sync(kFull, bad) && wlane() == 0) atomicOr(err, 1);
     }
 }
 
-// Rank-space weights: rwt[roff[r] + j] = weight of the j-th arc of order[r]
-// (the row order k_relabel keeps).  One warp per row.
+// Rank-space weights: rwt[p] for arc p of row r = weight of the same arc of
+// order[r] (k_relabel keeps the row order).
 __global__ void k_relabel_weights(const int64_t* row_ptr, const uint8_t* wt, const int32_t* order,
-                                  const int64_t* roff, uint8_t* rwt, int64_t n) {
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
-        const int32_t id = order[r];
-        const int64_t b = row_ptr[id], len = roff[r + 1] - roff[r];
-        for (int64_t j = wlane(); j < len; j += 32) rwt[roff[r] + j] = wt[b + j];
+                                  const int64_t* roff, uint8_t* rwt, int64_t n, int64_t nnz) {
+    __shared__ int64_t sh[2];
+    const int64_t ntiles = (nnz + kWTile - 1) / kWTile;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kWTile, p1 = min(nnz, p0 + kWTile);
+        tile_bounds(roff, n, p0, p1, sh);
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const int64_t r = row_of(roff, sh[0], sh[1], p);
+            rwt[p] = wt[row_ptr[order[r]] + (p - roff[r])];
+        }
     }
 }
 
-// Round d, one warp per receiver row v: each arc (v, a, w) gets its virtual
+// Round d, flat over the receivers' arcs: arc (v, a, w) gets its virtual
 // sender (the descriptor of a's frontier of round d - w, or the empty one),
-// and recv[v] = sum of |dL_{d-w}(a)| over the arcs whose smallest hub
-// outranks v (an upper bound on v's messages, as in k_mark).
-__global__ void k_w_pull(const int64_t* roff, const int32_t* rcol, const uint8_t* rwt, int64_t n, uint32_t d,
-                         int S, const uint64_t* fse_ring, const uint32_t* store, int32_t* vcol,
+// and recv[v] += |dL_{d-w}(a)| when that row's smallest hub outranks v (an
+// upper bound on v's messages, as in k_mark).  Lanes of a warp that share a
+// row add their counts first (one atomic per row and warp; counts are below
+// 2^24, a warp's sum below 2^29).  recv is zero on entry (k_collect clears
+// what it reads).
+__global__ void k_w_pull(const int64_t* roff, const int32_t* rcol, const uint8_t* rwt, int64_t n, int64_t nnz,
+                         uint32_t d, int S, const uint64_t* fse_ring, const uint32_t* store, int32_t* vcol,
                          unsigned long long* recv) {
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    __shared__ int64_t sh[2];
     const int32_t empty = (int32_t)((int64_t)S * n);
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nw) {
-        unsigned long long c = 0;
-        for (int64_t p = roff[v] + wlane(); p < roff[v + 1]; p += 32) {
-            const int32_t a = rcol[p];
-            const int r = (int)d - (int)rwt[p];
-            const int32_t idx = r >= 0 ? (int32_t)((int64_t)(r % S) * n + a) : empty;
-            vcol[p] = idx;
-            const uint64_t f = fse_ring[idx];
-            const uint32_t k = fcount(f);
-            if (k && (int64_t)store[fstart(f)] < v) c += k;
+    const int64_t ntiles = (nnz + kWTile - 1) / kWTile;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kWTile, p1 = min(nnz, p0 + kWTile);
+        tile_bounds(roff, n, p0, p1, sh);
+        for (int64_t q = p0; q < p1; q += blockDim.x) {  // uniform trip count: whole warps below
+            const int64_t p = q + threadIdx.x;
+            const bool ok = p < p1;
+            int64_t v = -1;
+            unsigned c = 0;
+            if (ok) {
+                v = row_of(roff, sh[0], sh[1], p);
+                const int32_t a = rcol[p];
+                const int r = (int)d - (int)rwt[p];
+                const int32_t idx = r >= 0 ? (int32_t)((int64_t)(r % S) * n + a) : empty;
+                vcol[p] = idx;
+                const uint64_t f = fse_ring[idx];
+                const uint32_t k = fcount(f);
+                if (k && (int64_t)store[fstart(f)] < v) c = k;
+            }
+            // the lanes of one row are consecutive: a segmented warp sum
+            const int lane = wlane();
+            const int incl = warp_incl_scan((int)c, lane);
+            const int64_t vprev = __shfl_up_sync(kFull, v, 1);
+            const int64_t vnext = __shfl_down_sync(kFull, v, 1);
+            const unsigned starts = __ballot_sync(kFull, lane == 0 || vprev != v);
+            const int first = 31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
+            const int before = __shfl_sync(kFull, incl - (int)c, first);
+            if (ok && (lane == 31 || vnext != v) && incl > before)
+                atomicAdd(recv + v, (unsigned long long)(incl - before));
         }
-        c = warp_sum(c);
-        if (wlane() == 0) recv[v] = c;
     }
 }
 
@@ -156,7 +196,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     const int sms = num_sms();
     const int flat_grid_cap = sms * 8;
     const int gflat = grid_for(n, kFlatThreads, flat_grid_cap);
-    const int gwarp = grid_for(n * 32, kWFlatThreads, flat_grid_cap);
+    const int gpull = grid_for((nnz + kWTile - 1) / kWTile, 1, flat_grid_cap);
     cudaEvent_t t_all0 = tm.on ? tm.mark() : nullptr;
     int64_t launches = 0;
 
@@ -207,7 +247,8 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
         pool.release(seen);
         if (herr[0]) return PLB_ERR_INVALID;
         if (nnz > 0) {  // arcs are symmetric and in range: compare the weights of both directions
-            k_check_weights<<<gwarp, kWFlatThreads, 0, s>>>(row_ptr, col, wt, n, err);
+            k_check_weights<<<grid_for((nnz + kWTile - 1) / kWTile, 1, flat_grid_cap), kWFlatThreads, 0, s>>>(
+                row_ptr, col, wt, n, nnz, err);
             PLB_CK(cudaGetLastError());
             PLB_CK(cudaMemcpyAsync(herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));
@@ -233,7 +274,8 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     if (nnz > 0) {
         k_relabel<<<grid_for((nnz + 2047) / 2048, 1, flat_grid_cap), kFlatThreads, 0, s>>>(row_ptr, col, order, inv,
                                                                                           roff, rcol, n, nnz);
-        k_relabel_weights<<<gwarp, kWFlatThreads, 0, s>>>(row_ptr, wt, order, roff, rwt, n);
+        k_relabel_weights<<<grid_for((nnz + kWTile - 1) / kWTile, 1, flat_grid_cap), kWFlatThreads, 0, s>>>(
+            row_ptr, wt, order, roff, rwt, n, nnz);
     }
     PLB_CK(cudaGetLastError());
     launches += 4 + scan_n;
@@ -258,6 +300,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     uint32_t* rbound = pool.alloc<uint32_t>(n);
     PLB_ALLOC_OK();
     PLB_CK(cudaMemsetAsync(ring, 0, sizeof(uint64_t) * ((size_t)S * n + 1), s));
+    PLB_CK(cudaMemsetAsync(recv, 0, sizeof(unsigned long long) * (size_t)n, s));
     // round 0: L(v) = dL_0(v) = {(v, 0)}; its frontier rows are store[0, n)
     k_init<<<gflat, kFlatThreads, 0, s>>>(roff, n, loff[0], lent[0], ring, store, A, ctr);
     k_top_init<<<flat_grid_cap, kFlatThreads, 0, s>>>(top, n);
@@ -404,7 +447,9 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
         uint64_t* fse_new = ring + (int64_t)(d % S) * n;
         cudaEvent_t r0 = tm.on ? tm.mark() : nullptr;
         k_w_round<<<1, 1, 0, s>>>(ctr, (uint32_t)d, (unsigned long long)base);
-        k_w_pull<<<gwarp, kWFlatThreads, 0, s>>>(roff, rcol, rwt, n, (uint32_t)d, S, ring, store, vcol, recv);
+        if (nnz > 0)
+            k_w_pull<<<gpull, kWFlatThreads, 0, s>>>(roff, rcol, rwt, n, nnz, (uint32_t)d, S, ring, store, vcol,
+                                                     recv);
         k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse_new, R, O1, rbound, nullptr, ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(ctr);
         launches += 4;
