@@ -388,8 +388,8 @@ def run_weighted(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"{args.workload} weights 1..7 (seed 2)", "n": g.n, "m": g.m,
-                       "labels": n_labels, "rounds": st0["rounds"], "max_dist": int(max(
-                           (d for d, a in enumerate(st0["accepted"]) if a > 0), default=0)),
+                       "labels": n_labels, "rounds": st0["rounds"], "max_dist": int(max(  # the per-round lists start at round 1
+                           (d + 1 for d, a in enumerate(st0["accepted"]) if a > 0), default=0)),
                        "l2": "flushed between steps (256 MB write)"},
             "roofline": {"bound": "hbm", "kernel": "gather+prune (k_gp_warp, k_gp_block)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak if peak else None,

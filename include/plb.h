@@ -85,7 +85,11 @@ typedef struct {
                                   Alg. 4): the rounds of batch i propagate only the hubs of
                                   ranks [i*batch_hubs, (i+1)*batch_hubs); same labels.
                                   Default 0 (one batch: VC-PLL, Alg. 3) */
-    int32_t reserved[7];
+    int32_t warp_stage_ratio;  /* warp tier: a receiver whose candidate bound times this is below
+                                  |L(v)| (a row with a probe table) looks L(v) up in v's row of
+                                  the probe index instead of staging it in shared memory;
+                                  0: always stage.  0..1024 (default 4) */
+    int32_t reserved[6];
 } plb_options;
 
 /* Opaque label set (library-owned device memory; free with plb_labels_free). */
@@ -184,7 +188,7 @@ int plb_build_directed(const plb_csr* g, const int32_t* vertex_order, const plb_
  * ignored (host-driven rounds, one batch).  Errors as plb_build, and
  * PLB_ERR_INVALID for a null weight array with arcs or a zero weight (always
  * checked) or, with validate, a weight that differs from its reverse arc's;
- * PLB_ERR_TOO_LARGE when (largest weight + 1) * n + 1 >= 2^31. */
+ * PLB_ERR_TOO_LARGE when (largest weight + 1) * 2^ceil(log2 n) + 1 >= 2^31. */
 int plb_build_weighted(const plb_csr* g, const uint8_t* weight, const int32_t* vertex_order,
                        const plb_options* opt, plb_stream stream, plb_labels** out);
 

@@ -120,6 +120,7 @@ void plb_default_options(plb_options* o) {
     o->use_graph = 0;
     o->profile = 0;
     o->batch_hubs = 0;
+    o->warp_stage_ratio = 4;
 }
 
 static int check_csr(const plb_csr* g, const int32_t* order) {
@@ -134,7 +135,8 @@ static int check_csr(const plb_csr* g, const int32_t* order) {
 static bool sane_options(const plb_options& o) {
     return o.warp_label_cap >= 1 && o.warp_label_cap <= 8192 && o.warp_cand_cap >= 1 && o.warp_cand_cap <= 4096 &&
            o.block_label_cap >= 1 && o.block_label_cap <= 16384 && o.block_cand_cap >= 1 &&
-           o.block_cand_cap <= 16384 && o.block_threads >= 64 && o.block_threads <= 256 && o.batch_hubs >= 0;
+           o.block_cand_cap <= 16384 && o.block_threads >= 64 && o.block_threads <= 256 && o.batch_hubs >= 0 &&
+           o.warp_stage_ratio >= 0 && o.warp_stage_ratio <= 1024;
 }
 
 static int empty_labels(plb_labels** out, cudaStream_t s) {

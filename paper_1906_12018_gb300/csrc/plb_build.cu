@@ -254,6 +254,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.gscratch = gacc;
         p.gscratch_words = std::max<int64_t>(n, 1);
         p.rbound = rbound;
+        p.stage_ratio = o.warp_stage_ratio;
         return p;
     };
     const int* skip = nullptr;  // graph mode: &ctr->done (scans of finished rounds do nothing)

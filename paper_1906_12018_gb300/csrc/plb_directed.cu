@@ -304,6 +304,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
         p.log_s = w_log_s;
         p.log_m = w_log_m;
         p.cand_limit = warp_cand;
+        p.stage_ratio = o.warp_stage_ratio;
         k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
         p.list = S.O1;
         p.list_n = &S.ctr->nO1;

@@ -153,11 +153,11 @@ __device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int6
             const uint64_t f = p.fse[a];
             const uint32_t n0 = fcount(f);
             if (n0) {
-                // the hubs of dL_{d-1}(a) are <= a (a itself only for d = 1):
-                // for a < hi the whole row lies below hi
+                // the hubs of a frontier row of sender a are <= a (a itself
+                // only in round 0): for a < hi the whole row lies below hi
                 const uint32_t* row = p.fhub + fstart(f);
                 const int64_t a0 = lo ? lower_bound_u32(row, n0, lo) : 0;
-                const int64_t a1 = (uint32_t)a < hi ? (int64_t)n0 : lower_bound_u32(row, n0, hi);
+                const int64_t a1 = sender_of(p, a) < hi ? (int64_t)n0 : lower_bound_u32(row, n0, hi);
                 st = (int64_t)fstart(f) + a0;
                 c = (int)(a1 - a0);
             }
@@ -289,11 +289,11 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
             const uint64_t f = p.fse[a];
             const uint32_t n0 = fcount(f);
             if (n0) {
-                // the hubs of dL_{d-1}(a) are <= a (a itself only for d = 1):
-                // for a < hi the whole row lies below hi
+                // the hubs of a frontier row of sender a are <= a (a itself
+                // only in round 0): for a < hi the whole row lies below hi
                 const uint32_t* row = p.fhub + fstart(f);
                 const int64_t a0 = lo ? lower_bound_u32(row, n0, lo) : 0;
-                const int64_t a1 = (uint32_t)a < hi ? (int64_t)n0 : lower_bound_u32(row, n0, hi);
+                const int64_t a1 = sender_of(p, a) < hi ? (int64_t)n0 : lower_bound_u32(row, n0, hi);
                 st = (int64_t)fstart(f) + a0;
                 c = (int)(a1 - a0);
             }
@@ -376,7 +376,8 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
 }
 
 // One warp per vertex (tables in shared memory):
-//  1. stage L(v) into the hub-keyed map M;
+//  1. stage L(v) into the hub-keyed map M (or, with few candidates against a
+//     long row, look L(v) up in v's row of the global probe index);
 //  2. gather the unique messages into the set S;
 //  3. compact S in place and check the candidates 32 at a time;
 //  4. append the accepted hubs (unsorted) to the new frontier.
@@ -403,18 +404,27 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
         // within the tier's limit), the map for |L(v)| (load <= 1/2)
         const uint32_t bnd = p.rbound[v];
         const int log_s = bnd <= (uint32_t)p.cand_limit ? max(5, ceil_log2_i64(2 * (int64_t)bnd)) : p.log_s;
-        const int log_m = max(5, ceil_log2_i64(2 * ll));
+        // L(v) lookups: the map staged in shared memory, or, for a receiver
+        // with few candidates against a long (indexed) row, v's row of the
+        // global probe index, which saves staging the whole row
+        const uint64_t hdv = (p.stage_ratio > 0 && ll >= kIndexMinLen &&
+                              (int64_t)bnd * p.stage_ratio < ll) ? p.hdesc[v] : 0ull;
+        const bool mglob = hdv != 0;
+        const int log_m = mglob ? (int)(hdv & 0xFFu) : max(5, ceil_log2_i64(2 * ll));
+        const uint32_t* Mv = mglob ? p.htab + (hdv >> 8) : M;
         for (int s = lane; s < (1 << log_s); s += 32) S[s] = kEmpty;
-        for (int s = lane; s < (1 << log_m); s += 32) M[s] = kEmpty;
+        if (!mglob)
+            for (int s = lane; s < (1 << log_m); s += 32) M[s] = kEmpty;
         if (lane == 0) {
             wsc[0] = 0;
             wsc[1] = 0;
         }
         __syncwarp();
-        for (int64_t j = lane; j < ll; j += 32) map_insert(M, log_m, p.lent[lb + j]);
+        if (!mglob)
+            for (int64_t j = lane; j < ll; j += 32) map_insert(M, log_m, p.lent[lb + j]);
         __syncwarp();
         const int64_t nb = p.roff[v], ne = p.roff[v + 1];
-        const bool ok = gather_range(p, nb, ne, 32, 0u, (uint32_t)v, S, log_s, M, log_m, p.cand_limit, &wsc[0],
+        const bool ok = gather_range(p, nb, ne, 32, 0u, (uint32_t)v, S, log_s, Mv, log_m, p.cand_limit, &wsc[0],
                                      (volatile int*)&wsc[1], c_msgs);
         __syncwarp();
         const int nS = *(volatile int*)&wsc[0];
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
         }
         if (lane == 0) {
             c_arcs += ne - nb;
-            c_staged += ll;
+            c_staged += mglob ? 0 : ll;
             c_vert += 1;
             c_uniq += nS;
         }
@@ -451,8 +461,8 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p, d, M, log_m, false, kWarpSideBMin, kWarpSideBShift, p.lent + lb, ll, h,
-                                             valid, c_probed, tv, c_pref);
+            const unsigned okm = check_chunk(p, d, Mv, log_m, mglob, kWarpSideBMin, kWarpSideBShift, p.lent + lb, ll,
+                                             h, valid, c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();

@@ -93,7 +93,16 @@ struct GpParams {
     const uint32_t* rbound;    // per receiver: candidate bound min(v, messages)
     const int64_t* ostart;     // per receiver: start of its new frontier row (the scan of the bounds),
                                // or null (rows reserved with an atomic cursor)
+    int stage_ratio;           // warp tier: L(v) read from v's probe table when rbound[v] * stage_ratio
+                               // < |L(v)| (0: always staged in shared memory)
+    int sender_bits;           // rcol holds frontier descriptor indices whose low sender_bits bits are
+                               // the sending vertex (weighted rounds), or 0: the vertex itself
 };
+
+// The sending vertex of an arc's descriptor index (see GpParams::sender_bits).
+__device__ __forceinline__ uint32_t sender_of(const GpParams& p, int32_t a) {
+    return p.sender_bits ? (uint32_t)a & ((1u << p.sender_bits) - 1u) : (uint32_t)a;
+}
 
 // Witness prefilter: for the kTopHubs highest-ranked hubs, every vertex x
 // keeps kTopLevels bitmasks C_t(x) = {w : w in L(x), d(w, x) <= t}, t = 1..

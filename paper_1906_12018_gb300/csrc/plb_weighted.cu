@@ -17,12 +17,13 @@
 //
 // The frontiers of the last maxw rounds stay live: descriptors in a ring of
 // S = maxw + 1 slots (slot r mod S holds round r), rows in one append-only
-// store in round order (a row start is an absolute offset).  Per round a pull
-// pass writes each arc's virtual sender, a + (r mod S) n for r = d - w >= 0
-// (else the always-empty descriptor S n), and counts the messages of every
-// receiver; the gather/prune kernels of the unweighted build then read the
-// frontier rows through the virtual senders unchanged.  Host-driven rounds,
-// one batch.
+// store in round order (a row start is an absolute offset); slot k's
+// descriptors sit at k << lgn, lgn = ceil(log2 n).  Per round a pull pass
+// writes each arc's virtual sender, (r mod S) << lgn | a for r = d - w >= 0
+// (else the always-empty descriptor S << lgn), and counts the messages of
+// every receiver; the gather/prune kernels of the unweighted build then read
+// the frontier rows through the virtual senders (GpParams::sender_bits = lgn
+// gives them the sending vertex back).  Host-driven rounds, one batch.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -109,17 +110,18 @@ __global__ void k_relabel_weights(const int64_t* row_ptr, const uint8_t* wt, con
 }
 
 // Round d, flat over the receivers' arcs: arc (v, a, w) gets its virtual
-// sender (the descriptor of a's frontier of round d - w, or the empty one),
+// sender ((d - w) mod S) << lgn | a, the descriptor of a's frontier of round
+// d - w (or the empty one when d < w),
 // and recv[v] += |dL_{d-w}(a)| when that row's smallest hub outranks v (an
 // upper bound on v's messages, as in k_mark).  Lanes of a warp that share a
 // row add their counts first (one atomic per row and warp; counts are below
 // 2^24, a warp's sum below 2^29).  recv is zero on entry (k_collect clears
 // what it reads).
 __global__ void k_w_pull(const int64_t* roff, const int32_t* rcol, const uint8_t* rwt, int64_t n, int64_t nnz,
-                         uint32_t d, int S, const uint64_t* fse_ring, const uint32_t* store, int32_t* vcol,
+                         uint32_t d, int S, int lgn, const uint64_t* fse_ring, const uint32_t* store, int32_t* vcol,
                          unsigned long long* recv) {
     __shared__ int64_t sh[2];
-    const int32_t empty = (int32_t)((int64_t)S * n);
+    const int32_t empty = (int32_t)((int64_t)S << lgn);
     const int64_t ntiles = (nnz + kWTile - 1) / kWTile;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int64_t p0 = t * kWTile, p1 = min(nnz, p0 + kWTile);
@@ -133,7 +135,7 @@ __global__ void k_w_pull(const int64_t* roff, const int32_t* rcol, const uint8_t
                 v = row_of(roff, sh[0], sh[1], p);
                 const int32_t a = rcol[p];
                 const int r = (int)d - (int)rwt[p];
-                const int32_t idx = r >= 0 ? (int32_t)((int64_t)(r % S) * n + a) : empty;
+                const int32_t idx = r >= 0 ? (int32_t)(((int64_t)(r % S) << lgn) | a) : empty;
                 vcol[p] = idx;
                 const uint64_t f = fse_ring[idx];
                 const uint32_t k = fcount(f);
@@ -227,7 +229,11 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     const int minw = nnz > 0 ? herr[2] : 1, maxw = nnz > 0 ? herr[3] : 1;
     if (minw < 1) return PLB_ERR_INVALID;
     const int S = maxw + 1;  // ring slots: rounds d - maxw .. d
-    if ((int64_t)S * n + 1 >= (int64_t(1) << 31)) return PLB_ERR_TOO_LARGE;
+    // slot r mod S of the ring holds round r's descriptors at (slot << lgn) + v
+    // (a power-of-two stride, so the gather reads the sender in the low bits)
+    const int lgn = std::max(1, ceil_log2_i64(n));
+    const int64_t ring_n = (int64_t)S << lgn;  // the empty descriptor sits at ring_n
+    if (ring_n + 1 >= (int64_t(1) << 31)) return PLB_ERR_TOO_LARGE;
     if (o.validate) {
         k_check_rowptr<<<grid_for(n + 1, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(row_ptr, n, nnz, err);
         int* seen = pool.alloc<int>(n);
@@ -285,7 +291,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     int64_t* loff[2] = {pool.alloc<int64_t>(n + 1), pool.alloc<int64_t>(n + 1)};
     uint32_t* lent[2] = {pool.alloc<uint32_t>(lcap[0]), pool.alloc<uint32_t>(lcap[1])};
     // frontier ring (S slots of n descriptors, then the empty one) and store
-    uint64_t* ring = pool.alloc<uint64_t>((int64_t)S * n + 1);
+    uint64_t* ring = pool.alloc<uint64_t>(ring_n + 1);
     int64_t scap = std::max<int64_t>(n + nnz + 1024, 4096);
     uint32_t* store = pool.alloc<uint32_t>(scap);
     uint32_t* top = pool.alloc<uint32_t>(n * kTopRow);
@@ -299,7 +305,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     int32_t* O1 = pool.alloc<int32_t>(n);
     uint32_t* rbound = pool.alloc<uint32_t>(n);
     PLB_ALLOC_OK();
-    PLB_CK(cudaMemsetAsync(ring, 0, sizeof(uint64_t) * ((size_t)S * n + 1), s));
+    PLB_CK(cudaMemsetAsync(ring, 0, sizeof(uint64_t) * ((size_t)ring_n + 1), s));
     PLB_CK(cudaMemsetAsync(recv, 0, sizeof(unsigned long long) * (size_t)n, s));
     // round 0: L(v) = dL_0(v) = {(v, 0)}; its frontier rows are store[0, n)
     k_init<<<gflat, kFlatThreads, 0, s>>>(roff, n, loff[0], lent[0], ring, store, A, ctr);
@@ -419,6 +425,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
         p.gscratch_words = std::max<int64_t>(n, 1);
         p.rbound = rbound;
         p.ostart = nullptr;
+        p.sender_bits = lgn;
         p.list = R;
         p.list_n = &ctr->nR;
         p.esc = O1;
@@ -426,6 +433,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
         p.log_s = w_log_s;
         p.log_m = w_log_m;
         p.cand_limit = warp_cand;
+        p.stage_ratio = o.warp_stage_ratio;
         k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
         p.list = O1;
         p.list_n = &ctr->nO1;
@@ -444,12 +452,12 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     int last = 0;  // last round that accepted labels (round 0: the self labels)
     int rounds = 0;
     for (int d = 1; d - last <= maxw; ++d) {
-        uint64_t* fse_new = ring + (int64_t)(d % S) * n;
+        uint64_t* fse_new = ring + ((int64_t)(d % S) << lgn);
         cudaEvent_t r0 = tm.on ? tm.mark() : nullptr;
         k_w_round<<<1, 1, 0, s>>>(ctr, (uint32_t)d, (unsigned long long)base);
         if (nnz > 0)
-            k_w_pull<<<gpull, kWFlatThreads, 0, s>>>(roff, rcol, rwt, n, nnz, (uint32_t)d, S, ring, store, vcol,
-                                                     recv);
+            k_w_pull<<<gpull, kWFlatThreads, 0, s>>>(roff, rcol, rwt, n, nnz, (uint32_t)d, S, lgn, ring, store,
+                                                     vcol, recv);
         k_collect<<<gflat, kFlatThreads, 0, s>>>(recv, roff, loff[cur], n, fse_new, R, O1, rbound, nullptr, ctr, lim);
         k_after_collect<<<1, 1, 0, s>>>(ctr);
         launches += 4;

@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
         ("use_graph", ctypes.c_int32),
         ("profile", ctypes.c_int32),
         ("batch_hubs", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("warp_stage_ratio", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
