@@ -379,7 +379,8 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
 //  1. stage L(v) into the hub-keyed map M (or, with few candidates against a
 //     long row, look L(v) up in v's row of the global probe index);
 //  2. gather the unique messages into the set S;
-//  3. compact S in place and check the candidates 32 at a time;
+//  3. compact S in place (L(v)'s sorted row behind it when it fits) and
+//     check the candidates 32 at a time;
 //  4. append the accepted hubs (unsorted) to the new frontier.
 // A vertex whose unique candidates exceed cand_limit goes to the block tier.
 __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
@@ -452,6 +453,15 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             nc += __popc(m);
         }
         __syncwarp();
+        // L(v)'s sorted row, copied behind the candidates (the set's slots
+        // past nc are free now) when it fits: the checks' binary searches in
+        // L(v) and their side-B scans of it then read shared memory
+        const uint32_t* lvp = p.lent + lb;
+        if (nc > 0 && (int64_t)nc + ll <= S_CAP) {
+            uint32_t* lvs = S + (S_CAP - ll);
+            for (int64_t j = lane; j < ll; j += 32) lvs[j] = p.lent[lb + j];
+            lvp = lvs;
+        }
         // distance checks, 32 candidates at a time; survivors compacted in place
         uint32_t* tv = tvs + wib * kTopRow;
         if (nc > 0) stage_exact_levels(p.top, v, tv, lane, 32);
@@ -461,8 +471,8 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p, d, Mv, log_m, mglob, kWarpSideBMin, kWarpSideBShift, p.lent + lb, ll,
-                                             h, valid, c_probed, tv, c_pref);
+            const unsigned okm = check_chunk(p, d, Mv, log_m, mglob, kWarpSideBMin, kWarpSideBShift, lvp, ll, h,
+                                             valid, c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
