@@ -52,7 +52,7 @@ def gather_prune_bytes(st: dict, n: int) -> int:
 # profiles/ (valid only while the kernel sources hash to the recorded value).
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "gp_traffic_chunglu20.md")
 KERNEL_SOURCES = ("paper_1906_12018_gb300/csrc/plb_gather.cu", "paper_1906_12018_gb300/csrc/plb_kernels.cuh",
-                  "paper_1906_12018_gb300/csrc/plb_internal.cuh")
+                  "paper_1906_12018_gb300/csrc/plb_internal.cuh", "paper_1906_12018_gb300/csrc/plb_round.cu")
 
 
 def kernel_source_hash() -> str:

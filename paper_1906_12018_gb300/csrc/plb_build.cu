@@ -116,6 +116,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int32_t* O1 = pool.alloc<int32_t>(n);
     int32_t* O2 = pool.alloc<int32_t>(n);  // warp-tier escalations when the two tiers run concurrently
     uint32_t* rbound = pool.alloc<uint32_t>(n);
+    uint32_t* cur1 = pool.alloc<uint32_t>(n);  // round 1: per-row write cursors
     int64_t* aoff = pool.alloc<int64_t>(n + 1);
     PLB_ALLOC_OK();
     PLB_CK(cudaMemsetAsync(recv, 0, sizeof(unsigned long long) * std::max<int64_t>(n, 1), s));
@@ -372,12 +373,15 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             // round 1 needs no frontier step and no check (k_round1); the
             // new-frontier buffer holds every arc
             k_set_round<<<1, 1, 0, s>>>(ctr, 1u);
-            const int g1w = grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap);
-            k_round1_count<<<g1w, kFlatThreads, 0, s>>>(roff, rcol, n, (int32_t)batch_lo, (int32_t)batch_hi, tmp64,
-                                                       ctr);
+            const int g1 = grid_for((nnz + 2047) / 2048, 1, flat_grid_cap);
+            PLB_CK(cudaMemsetAsync(tmp64, 0, sizeof(int64_t) * (n + 1), s));
+            PLB_CK(cudaMemsetAsync(cur1, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
+            if (nnz > 0)
+                k_round1_count<<<g1, kFlatThreads, 0, s>>>(roff, rcol, n, nnz, (int32_t)batch_lo, (int32_t)batch_hi,
+                                                          reinterpret_cast<unsigned long long*>(tmp64), ctr);
             PLB_CK(exclusive_scan_i64(tmp64, tmp64, n, scan_scr, s));
-            k_round1<<<g1w, kFlatThreads, 0, s>>>(roff, rcol, n, (int32_t)batch_lo, (int32_t)batch_hi, tmp64,
-                                                 fse[nxt], fhub[nxt], (unsigned long long)fcap[nxt], ctr);
+            k_round1<<<g1, kFlatThreads, 0, s>>>(roff, rcol, n, nnz, (int32_t)batch_lo, (int32_t)batch_hi, tmp64,
+                                                cur1, fse[nxt], fhub[nxt], (unsigned long long)fcap[nxt], ctr);
             st.launches += 3 + scan_n;
             PLB_CK(cudaGetLastError());
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));

@@ -252,6 +252,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
     const int grid_b = sms * std::max(1, occ_b);
     int32_t* big = pool.alloc<int32_t>(n);
     int32_t* giant = pool.alloc<int32_t>(n);
+    uint32_t* cur1 = pool.alloc<uint32_t>(n);  // round 1: per-row write cursors
     const int sort_blocks = 8;
     const int64_t sort_words = pow2_at_least(std::max<int64_t>(n, 1));
     uint32_t* sortscr = pool.alloc<uint32_t>(sort_words * sort_blocks);
@@ -352,11 +353,15 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
             k_set_round<<<1, 1, 0, s>>>(S.ctr, (uint32_t)d);
             launches += 1;
             if (d == 1) {
-                const int g1w = grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap);
-                k_round1_count<<<g1w, kFlatThreads, 0, s>>>(S.g_off, S.g_col, n, 0, (int32_t)n, tmp64, S.ctr);
+                const int g1 = grid_for((nnz + 2047) / 2048, 1, flat_grid_cap);
+                PLB_CK(cudaMemsetAsync(tmp64, 0, sizeof(int64_t) * (n + 1), s));
+                PLB_CK(cudaMemsetAsync(cur1, 0, sizeof(uint32_t) * std::max<int64_t>(n, 1), s));
+                if (nnz > 0)
+                    k_round1_count<<<g1, kFlatThreads, 0, s>>>(S.g_off, S.g_col, n, nnz, 0, (int32_t)n,
+                                                              reinterpret_cast<unsigned long long*>(tmp64), S.ctr);
                 PLB_CK(exclusive_scan_i64(tmp64, tmp64, n, scan_scr, s));
-                k_round1<<<g1w, kFlatThreads, 0, s>>>(S.g_off, S.g_col, n, 0, (int32_t)n, tmp64, S.fse[x], S.fhub[x],
-                                                     (unsigned long long)S.fcap[x], S.ctr);
+                k_round1<<<g1, kFlatThreads, 0, s>>>(S.g_off, S.g_col, n, nnz, 0, (int32_t)n, tmp64, cur1, S.fse[x],
+                                                    S.fhub[x], (unsigned long long)S.fcap[x], S.ctr);
                 launches += 2 + scan_n;
                 PLB_CK(cudaGetLastError());
                 continue;

@@ -78,6 +78,23 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
     return x;
 }
 
+// Runs of equal keys over the lanes (each key's lanes consecutive, as the
+// rows of consecutive arcs): returns, in every lane, the sum of x over the
+// lane's run, which holds lanes *first..*last.  All 32 lanes call it.
+__device__ __forceinline__ int run_sum(int64_t key, int x, int lane, int* first, int* last) {
+    const int incl = warp_incl_scan(x, lane);
+    const int64_t kprev = __shfl_up_sync(kFull, key, 1);
+    const int64_t knext = __shfl_down_sync(kFull, key, 1);
+    const unsigned starts = __ballot_sync(kFull, lane == 0 || kprev != key);
+    const unsigned ends = __ballot_sync(kFull, lane == 31 || knext != key);
+    const int f = 31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));  // last run start at or below the lane
+    const int l = __ffs(ends & (0xFFFFFFFFu << lane)) - 1;            // first run end at or above it
+    const int before = __shfl_sync(kFull, incl - x, f);
+    *first = f;
+    *last = l;
+    return __shfl_sync(kFull, incl, l) - before;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

@@ -258,40 +258,53 @@ __global__ void k_after_collect(RoundCounters* ctr) {
 // (each sends its label (a, 0)), they are distinct, and none is pruned: a
 // witness w of (a, 1) at v would need d(w, v) + d(w, a) <= 1, so w = v or
 // w = a, but (v, .) is not a hub of a (v > a) and (a, .) not yet one of v.
-// So dL_1(v) = N(v) n [s, min(e, v)): one warp per vertex appends it
-// (unsorted; the merge step sorts the rows), clears the other frontier
-// descriptors and restarts the active list.  Counted like the general round:
+// So dL_1(v) = N(v) n [s, min(e, v)): it is appended (unsorted; the merge
+// step sorts the rows), the other frontier descriptors are cleared and the
+// active list restarts.  Counted like the general round:
 // one message, one unique candidate and one accepted label per such neighbour.
-// Count pass: cnt[v] = |N(v) n [s, min(e, v))|, one warp per vertex.
-__global__ void k_round1_count(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
-                               int64_t* cnt, const RoundCounters* ctr) {
+// Both passes run flat over tiles of arcs (a hub's row is spread over many
+// warps instead of one), each arc's row found by binary search in the tile's
+// row range.
+// Count pass: cnt[v] = |N(v) n [s, min(e, v))| (cnt zero on entry; one
+// atomic per row and warp).
+__global__ void k_round1_count(const int64_t* roff, const int32_t* rcol, int64_t n, int64_t nnz, int32_t s,
+                               int32_t e, unsigned long long* cnt, const RoundCounters* ctr) {
+    __shared__ int64_t sh_r[2];
     if (ctr->done) return;
     const int lane = lane_id();
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp0; v < n; v += nwarps) {
-        const int64_t nb = roff[v], ne = roff[v + 1];
-        int c = 0;
-        for (int64_t j0 = nb; j0 < ne; j0 += 128) {  // four independent loads per lane
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t j = j0 + 32 * u + lane;
-                if (j < ne) {
-                    const int32_t a = rcol[j];
-                    c += (a >= s && a < e && a < v) ? 1 : 0;
-                }
+    const int64_t ntiles = (nnz + kTileItems - 1) / kTileItems;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kTileItems, p1 = min(nnz, p0 + kTileItems);
+        __syncthreads();
+        if (threadIdx.x == 0) tile_rows(roff, n, p0, p1, &sh_r[0], &sh_r[1]);
+        __syncthreads();
+        const int64_t r0 = sh_r[0], r1 = sh_r[1];
+        for (int64_t q = p0; q < p1; q += blockDim.x) {  // uniform trip count: whole warps below
+            const int64_t p = q + threadIdx.x;
+            const bool ok = p < p1;
+            int64_t v = -1;
+            int c = 0;
+            if (ok) {
+                v = row_of(roff, r0, r1, p);
+                const int32_t a = rcol[p];
+                c = (a >= s && a < e && (int64_t)a < v) ? 1 : 0;
             }
+            int first, last;
+            const int sum = run_sum(v, c, lane, &first, &last);
+            if (ok && lane == last && sum > 0) atomicAdd(cnt + v, (unsigned long long)sum);
         }
-        c = warp_sum(c);
-        if (lane == 0) cnt[v] = c;
     }
 }
 
 // Write pass: row v of the new frontier at start[v] (the exclusive scan of
-// the counts: no shared cursor), start[n] entries in all.
-__global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
-                         const int64_t* start, uint64_t* fse_new, uint32_t* fhub_new, unsigned long long fcap,
-                         RoundCounters* ctr) {
+// the counts: no shared cursor), start[n] entries in all; within a row the
+// entries are placed by the per-row cursor cur[v] (zero on entry; one atomic
+// per row and warp).  Then, per vertex, the frontier descriptor and the
+// counters.
+__global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, int64_t nnz, int32_t s, int32_t e,
+                         const int64_t* start, uint32_t* cur, uint64_t* fse_new, uint32_t* fhub_new,
+                         unsigned long long fcap, RoundCounters* ctr) {
+    __shared__ int64_t sh_r[2];
     if (ctr->done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->nA_saved = ctr->nA;
@@ -301,30 +314,44 @@ __global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, in
     }
     if ((unsigned long long)start[n] > fcap) return;
     const int lane = lane_id();
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t ntiles = (nnz + kTileItems - 1) / kTileItems;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * kTileItems, p1 = min(nnz, p0 + kTileItems);
+        __syncthreads();
+        if (threadIdx.x == 0) tile_rows(roff, n, p0, p1, &sh_r[0], &sh_r[1]);
+        __syncthreads();
+        const int64_t r0 = sh_r[0], r1 = sh_r[1];
+        for (int64_t q = p0; q < p1; q += blockDim.x) {
+            const int64_t p = q + threadIdx.x;
+            const bool ok = p < p1;
+            int64_t v = -1;
+            int32_t a = 0;
+            bool up = false;
+            if (ok) {
+                v = row_of(roff, r0, r1, p);
+                a = rcol[p];
+                up = a >= s && a < e && (int64_t)a < v;
+            }
+            int first, last;
+            const int cnt = run_sum(v, up ? 1 : 0, lane, &first, &last);
+            const unsigned upm = __ballot_sync(kFull, up);
+            unsigned base = 0;
+            if (ok && lane == first && cnt > 0) base = atomicAdd(cur + v, (unsigned)cnt);
+            base = __shfl_sync(kFull, base, first);
+            if (up) {
+                const unsigned below = upm & ((1u << lane) - 1u) & ~((1u << first) - 1u);
+                fhub_new[start[v] + base + __popc(below)] = (uint32_t)a;
+            }
+        }
+    }
     unsigned long long c_acc = 0, c_arcs = 0, c_recv = 0;
-    for (int64_t v = warp0; v < n; v += nwarps) {
-        const int64_t nb = roff[v], ne = roff[v + 1];
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t st = start[v];
-        const int c = (int)(start[v + 1] - st);
-        if (c == 0) {
-            if (lane == 0) fse_new[v] = 0;
-            continue;
-        }
-        int o = 0;
-        for (int64_t j0 = nb; j0 < ne; j0 += 32) {
-            const int64_t j = j0 + lane;
-            const int32_t a = j < ne ? rcol[j] : INT32_MAX;
-            const bool up = a >= s && a < e && a < v;
-            const unsigned m = __ballot_sync(kFull, up);
-            if (up) fhub_new[st + o + __popc(m & ((1u << lane) - 1u))] = (uint32_t)a;
-            o += __popc(m);
-        }
-        if (lane == 0) {
-            fse_new[v] = fpack((uint64_t)st, (uint32_t)c);
-            c_acc += c;
-            c_arcs += ne - nb;
+        const int64_t c = start[v + 1] - st;
+        fse_new[v] = c ? fpack((uint64_t)st, (uint32_t)c) : 0ull;
+        if (c) {
+            c_acc += (unsigned long long)c;
+            c_arcs += (unsigned long long)(roff[v + 1] - roff[v]);
             c_recv += 1;
         }
     }

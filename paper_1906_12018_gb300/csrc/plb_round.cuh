@@ -29,11 +29,11 @@ __global__ void k_collect(unsigned long long* recv, const int64_t* roff, const i
                           RoundCounters* ctr, TierLimits lim);
 __global__ void k_after_collect(RoundCounters* ctr);
 __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n);
-__global__ void k_round1_count(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
-                               int64_t* cnt, const RoundCounters* ctr);
-__global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, int32_t s, int32_t e,
-                         const int64_t* start, uint64_t* fse_new, uint32_t* fhub_new, unsigned long long fcap,
-                         RoundCounters* ctr);
+__global__ void k_round1_count(const int64_t* roff, const int32_t* rcol, int64_t n, int64_t nnz, int32_t s,
+                               int32_t e, unsigned long long* cnt, const RoundCounters* ctr);
+__global__ void k_round1(const int64_t* roff, const int32_t* rcol, int64_t n, int64_t nnz, int32_t s, int32_t e,
+                         const int64_t* start, uint32_t* cur, uint64_t* fse_new, uint32_t* fhub_new,
+                         unsigned long long fcap, RoundCounters* ctr);
 __global__ void k_gp_warp(GpParams p);
 __global__ void k_gp_block(GpParams p);
 __global__ void k_index_size(const int64_t* loff, int64_t n, int64_t* hsz, const RoundCounters* ctr);

@@ -141,16 +141,11 @@ __global__ void k_w_pull(const int64_t* roff, const int32_t* rcol, const uint8_t
                 const uint32_t k = fcount(f);
                 if (k && (int64_t)store[fstart(f)] < v) c = k;
             }
-            // the lanes of one row are consecutive: a segmented warp sum
+            // the lanes of one row are consecutive: one atomic per run
             const int lane = wlane();
-            const int incl = warp_incl_scan((int)c, lane);
-            const int64_t vprev = __shfl_up_sync(kFull, v, 1);
-            const int64_t vnext = __shfl_down_sync(kFull, v, 1);
-            const unsigned starts = __ballot_sync(kFull, lane == 0 || vprev != v);
-            const int first = 31 - __clz(starts & (0xFFFFFFFFu >> (31 - lane)));
-            const int before = __shfl_sync(kFull, incl - (int)c, first);
-            if (ok && (lane == 31 || vnext != v) && incl > before)
-                atomicAdd(recv + v, (unsigned long long)(incl - before));
+            int first, last;
+            const int sum = run_sum(v, (int)c, lane, &first, &last);
+            if (ok && lane == last && sum > 0) atomicAdd(recv + v, (unsigned long long)sum);
         }
     }
 }
