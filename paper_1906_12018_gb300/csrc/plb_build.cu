@@ -117,6 +117,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     int32_t* O2 = pool.alloc<int32_t>(n);  // warp-tier escalations when the two tiers run concurrently
     uint32_t* rbound = pool.alloc<uint32_t>(n);
     uint32_t* cur1 = pool.alloc<uint32_t>(n);  // round 1: per-row write cursors
+    int32_t* U = pool.alloc<int32_t>(n);       // vertices whose new row the block tier wrote unsorted
     int64_t* aoff = pool.alloc<int64_t>(n + 1);
     PLB_ALLOC_OK();
     PLB_CK(cudaMemsetAsync(recv, 0, sizeof(unsigned long long) * std::max<int64_t>(n, 1), s));
@@ -256,6 +257,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.gscratch_words = std::max<int64_t>(n, 1);
         p.rbound = rbound;
         p.stage_ratio = o.warp_stage_ratio;
+        p.unsorted = U;
         return p;
     };
     const int* skip = nullptr;  // graph mode: &ctr->done (scans of finished rounds do nothing)
@@ -338,7 +340,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     auto launch_merge = [&](int c, int x) -> cudaError_t {
         k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[c], fse[x], n, tmp64, A, ctr);
         // sort the new frontier rows (appended unsorted by the gather/prune kernels)
-        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[x], fhub[x], A, ctr, big, giant);
+        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[x], fhub[x], A, U, 1, ctr, big, giant);
         k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(fse[x], fhub[x], big, &ctr->nBig, nullptr,
                                                                         0, ctr);
         k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[x], fhub[x], giant, &ctr->nGiant,

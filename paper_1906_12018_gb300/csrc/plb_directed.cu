@@ -41,6 +41,7 @@ struct Side {
     int32_t* A = nullptr;
     int32_t* R = nullptr;
     int32_t* O1 = nullptr;
+    int32_t* U = nullptr;           // vertices whose new row the block tier wrote unsorted
     uint32_t* rbound = nullptr;
     int64_t* aoff = nullptr;
     RoundCounters* ctr = nullptr;
@@ -177,6 +178,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
         S.A = pool.alloc<int32_t>(n);
         S.R = pool.alloc<int32_t>(n);
         S.O1 = pool.alloc<int32_t>(n);
+        S.U = pool.alloc<int32_t>(n);
         S.rbound = pool.alloc<uint32_t>(n);
         S.aoff = pool.alloc<int64_t>(n + 1);
         PLB_ALLOC_OK();
@@ -306,6 +308,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
         p.log_m = w_log_m;
         p.cand_limit = warp_cand;
         p.stage_ratio = o.warp_stage_ratio;
+        p.unsorted = S.U;
         k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
         p.list = S.O1;
         p.list_n = &S.ctr->nO1;
@@ -321,7 +324,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
     auto merge = [&](Side& S) -> cudaError_t {
         const int c = S.cur, x = c ^ 1;
         k_next_active<<<gflat, kFlatThreads, 0, s>>>(S.loff[c], S.fse[x], n, tmp64, S.A, S.ctr);
-        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(S.fse[x], S.fhub[x], S.A, S.ctr, big, giant);
+        k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(S.fse[x], S.fhub[x], S.A, S.U, 1, S.ctr, big, giant);
         k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(S.fse[x], S.fhub[x], big, &S.ctr->nBig,
                                                                         nullptr, 0, S.ctr);
         k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(S.fse[x], S.fhub[x], giant,

@@ -5,7 +5,8 @@
 // (h, d) iff no common hub w has d(w, v) + d(w, h) <= d).
 //   k_gp_warp   one vertex per warp, tables in shared memory;
 //   k_gp_block  one vertex per 256-thread block, any size.
-// Both append the accepted hubs (unsorted) to the new frontier.
+// Both append the accepted hubs to the new frontier: the warp tier sorted,
+// the block tier unsorted (it lists those vertices for the row sort).
 #include "plb_kernels.cuh"
 #include "plb_round.cuh"
 
@@ -381,7 +382,7 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
 //  2. gather the unique messages into the set S;
 //  3. compact S in place (L(v)'s sorted row behind it when it fits) and
 //     check the candidates 32 at a time;
-//  4. append the accepted hubs (unsorted) to the new frontier.
+//  4. sort the accepted hubs and append them to the new frontier.
 // A vertex whose unique candidates exceed cand_limit goes to the block tier.
 __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
     extern __shared__ uint32_t sm[];
@@ -475,6 +476,30 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
                                              valid, c_probed, tv, c_pref);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
+            __syncwarp();
+        }
+        // the new row leaves sorted by hub rank: bitonic sort of S[0, nacc)
+        // (nacc <= cand_limit, a power of two at most half the set's slots)
+        if (nacc > 1) {
+            if (nacc <= 32) {
+                uint32_t x = lane < nacc ? S[lane] : kEmpty;
+#pragma unroll
+                for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+                    for (int j = k >> 1; j > 0; j >>= 1) {
+                        const uint32_t y = __shfl_xor_sync(kFull, x, j);
+                        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+                        x = (lower == up) ? min(x, y) : max(x, y);
+                    }
+                }
+                if (lane < nacc) S[lane] = x;
+            } else {
+                int P = 64;
+                while (P < nacc) P <<= 1;
+                for (int j = nacc + lane; j < P; j += 32) S[j] = kEmpty;
+                __syncwarp();
+                group_bitonic_sort(S, P, lane, 32, WarpSync());
+            }
             __syncwarp();
         }
         if (nacc > 0) {
@@ -672,7 +697,10 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
         const unsigned long long start = *(volatile unsigned long long*)(sh + SH_START);
         if (start + total_acc <= p.fcap) {
             for (int64_t j = tid; j < total_acc; j += nthr) p.fhub_new[start + j] = gacc[j];
-            if (tid == 0) p.fse_new[v] = fpack(start, (uint32_t)total_acc);
+            if (tid == 0) {
+                p.fse_new[v] = fpack(start, (uint32_t)total_acc);
+                if (p.unsorted && total_acc > 1) p.unsorted[atomicAdd(&p.ctr->nU, 1)] = v;  // sorted after the round
+            }
         } else if (tid == 0) {
             p.ctr->fovf = 1;
         }

@@ -135,19 +135,22 @@ __device__ __forceinline__ int64_t row_of(const int64_t* off, int64_t lo, int64_
 }
 
 // Bitonic sort of a[0..P) (P a power of two) by a group of nthreads threads.
+// Each step runs over the P/2 compare-exchange pairs (i, i + j), i the pair
+// index t with a zero bit inserted at bit log2(j): no idle half of the
+// threads.
 template <typename Sync>
 __device__ void group_bitonic_sort(uint32_t* a, int P, int tid, int nthreads, Sync sync) {
+    const int half = P >> 1;
     for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < P; i += nthreads) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const uint32_t x = a[i], y = a[l];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        a[i] = y;
-                        a[l] = x;
-                    }
+            for (int t = tid; t < half; t += nthreads) {
+                const int i = 2 * t - (t & (j - 1));
+                const int l = i + j;
+                const uint32_t x = a[i], y = a[l];
+                const bool up = (i & k) == 0;
+                if ((x > y) == up) {
+                    a[i] = y;
+                    a[l] = x;
                 }
             }
             sync();

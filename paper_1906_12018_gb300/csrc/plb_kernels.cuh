@@ -12,8 +12,10 @@
 //                  Alg. 3: unique messages, then d < min over common hubs).
 //   k_gp_block     the same with one vertex per block (any size: hub-range
 //                  passes, a byte map for the top hubs).
-//   k_sort_rows_*, k_merge_*
-//                  L(v) <- L(v) U dL_d(v), keeping rows sorted by hub rank;
+//   k_sort_rows_*  rows of the new frontier that were written unsorted (round
+//                  1; the block tier's) sorted by hub rank (the warp tier
+//                  writes its rows sorted);
+//   k_merge_*      L(v) <- L(v) U dL_d(v), keeping rows sorted by hub rank;
 //                  then the probe index of L is rebuilt (k_index_*).
 #pragma once
 
@@ -30,6 +32,7 @@ struct RoundCounters {
     unsigned long long prefiltered; // candidates pruned by the top-hub witness prefilter
     int nR, nO1, nO2;             // receivers: warp tier, block tier (nO2 unused)
     int nBig, nGiant;             // new frontier rows too long for a warp / for shared memory to sort
+    int nU;                       // vertices whose new frontier row was written unsorted (block tier)
     int nA;                       // next active list (kept across the per-round reset)
     int nO1_base, nO2_base;       // tier-list sizes made by k_collect (for reruns)
     int fovf;                     // new-frontier buffer overflow
@@ -95,6 +98,8 @@ struct GpParams {
                                // or null (rows reserved with an atomic cursor)
     int stage_ratio;           // warp tier: L(v) read from v's probe table when rbound[v] * stage_ratio
                                // < |L(v)| (0: always staged in shared memory)
+    int32_t* unsorted;         // block tier: list of the vertices whose new row it wrote (unsorted;
+                               // count ctr->nU), or null (every new row is sorted after the round)
     int sender_bits;           // rcol holds frontier descriptor indices whose low sender_bits bits are
                                // the sending vertex (weighted rounds), or 0: the vertex itself
 };

@@ -378,6 +378,7 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
         ctr->cursor = 0;
         ctr->accepted = 0;
         ctr->fovf = 0;
+        ctr->nU = 0;
         ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = 0;
         ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;
     }
@@ -523,13 +524,19 @@ constexpr int kWarpSortMax = 1024;
 constexpr int kSortWarps = 8;
 constexpr int kBlockSortSmem = 16384;
 
+// The rows taken: every new row (A, ctr->nA) when U is null or, with
+// r1_all, in round 1 (whose rows k_round1 writes unsorted); else the rows the
+// block tier listed in U (ctr->nU).
 __global__ void __launch_bounds__(kSortWarps * 32) k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new,
-                                                                   const int32_t* A, RoundCounters* ctr,
-                                                                   int32_t* big, int32_t* giant) {
+                                                                   const int32_t* A, const int32_t* U, int r1_all,
+                                                                   RoundCounters* ctr, int32_t* big,
+                                                                   int32_t* giant) {
     __shared__ uint32_t buf[kSortWarps][kWarpSortMax];
     const int lane = lane_id(), w = threadIdx.x >> 5;
     if (ctr->done) return;
-    const int nA = ctr->nA;
+    const bool all = U == nullptr || (r1_all && ctr->d == 1);
+    const int nA = all ? ctr->nA : ctr->nU;
+    if (!all) A = U;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nA; i += nw) {
         const int32_t v = A[i];
@@ -727,7 +734,7 @@ __global__ void k_g_finish(RoundCounters* ctr) {
     ctr->cursor = ctr->accepted = ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = 0;
     ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;
     ctr->bound_sum = ctr->prefiltered = 0;
-    ctr->nR = ctr->nO1 = ctr->nO2 = ctr->nBig = ctr->nGiant = 0;
+    ctr->nR = ctr->nO1 = ctr->nO2 = ctr->nBig = ctr->nGiant = ctr->nU = 0;
     ctr->nO1_base = ctr->nO2_base = ctr->fovf = 0;
 }
 

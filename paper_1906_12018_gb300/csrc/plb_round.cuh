@@ -51,8 +51,8 @@ __global__ void k_g_finish(RoundCounters* ctr);
 __global__ void k_g_cond(const RoundCounters* ctr, cudaGraphConditionalHandle h);
 __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int64_t n, int64_t* newlen, int32_t* A,
                               RoundCounters* ctr);
-__global__ void k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* A, RoundCounters* ctr,
-                                 int32_t* big, int32_t* giant);
+__global__ void k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* A, const int32_t* U,
+                                 int r1_all, RoundCounters* ctr, int32_t* big, int32_t* giant);
 __global__ void k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* big, const int* nbig,
                                   uint32_t* scratch, int64_t scratch_words, const RoundCounters* ctr);
 __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,

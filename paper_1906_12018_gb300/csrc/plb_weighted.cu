@@ -165,6 +165,7 @@ __global__ void k_w_rerun(RoundCounters* ctr, uint64_t* fse_new, int64_t n, unsi
         ctr->cursor = base;
         ctr->accepted = 0;
         ctr->fovf = 0;
+        ctr->nU = 0;
         ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = ctr->prefiltered = 0;
         ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;
     }
@@ -298,6 +299,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     int32_t* A = pool.alloc<int32_t>(n);
     int32_t* R = pool.alloc<int32_t>(n);
     int32_t* O1 = pool.alloc<int32_t>(n);
+    int32_t* U = pool.alloc<int32_t>(n);  // vertices whose new row the block tier wrote unsorted
     uint32_t* rbound = pool.alloc<uint32_t>(n);
     PLB_ALLOC_OK();
     PLB_CK(cudaMemsetAsync(ring, 0, sizeof(uint64_t) * ((size_t)ring_n + 1), s));
@@ -429,6 +431,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
         p.log_m = w_log_m;
         p.cand_limit = warp_cand;
         p.stage_ratio = o.warp_stage_ratio;
+        p.unsorted = U;
         k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
         p.list = O1;
         p.list_n = &ctr->nO1;
@@ -523,7 +526,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
                 PLB_ALLOC_OK();
             }
             k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[cur], fse_new, n, tmp64, A, ctr);
-            k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse_new, store, A, ctr, big, giant);
+            k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse_new, store, A, U, 0, ctr, big, giant);
             k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(fse_new, store, big, &ctr->nBig,
                                                                             nullptr, 0, ctr);
             k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse_new, store, giant,
