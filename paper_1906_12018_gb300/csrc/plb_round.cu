@@ -599,9 +599,18 @@ __global__ void __launch_bounds__(1024) k_sort_rows_block(const uint64_t* fse_ne
 }
 
 // Old entries move to their place in the merged row: flat over old entries.
+// A tile of entries that spans at most kMergeRows rows stages those rows'
+// old and new offsets and new-frontier descriptors in shared memory (each
+// entry's row is a binary search there); a tile over more rows reads them
+// from global memory.
+constexpr int kMergeRows = 512;
+
 __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
                             const uint64_t* fse_new, const uint32_t* fhub_new, int64_t n, const RoundCounters* ctr) {
     __shared__ int64_t sh_r[2];
+    __shared__ int64_t s_off[kMergeRows + 1];
+    __shared__ int64_t s_noff[kMergeRows];
+    __shared__ uint64_t s_f[kMergeRows];
     if (ctr->done) return;
     const int64_t total = loff[n];
     const int64_t ntiles = (total + kTileItems - 1) / kTileItems;
@@ -611,11 +620,37 @@ __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int
         if (threadIdx.x == 0) tile_rows(loff, n, p0, p1, &sh_r[0], &sh_r[1]);
         __syncthreads();
         const int64_t r0 = sh_r[0], r1 = sh_r[1];
+        const int64_t rows = r1 - r0 + 1;
+        const int nr = rows <= kMergeRows ? (int)rows : kMergeRows + 1;
+        const bool staged = nr <= kMergeRows;
+        if (staged) {
+            for (int i = threadIdx.x; i <= nr; i += blockDim.x) s_off[i] = loff[r0 + i];
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+                s_noff[i] = loff_new[r0 + i];
+                s_f[i] = fse_new[r0 + i];
+            }
+        }
+        __syncthreads();
         for (int64_t q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
-            const int64_t v = row_of(loff, r0, r1, q);
+            int64_t ob, nb;
+            uint64_t f;
+            if (staged) {
+                int lo = 0, hi = nr - 1;  // last row of the tile whose offset is <= q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                ob = s_off[lo];
+                nb = s_noff[lo];
+                f = s_f[lo];
+            } else {
+                const int64_t v = row_of(loff, r0, r1, q);
+                ob = loff[v];
+                nb = loff_new[v];
+                f = fse_new[v];
+            }
             const uint32_t e = lent[q];
-            const uint64_t f = fse_new[v];
-            int64_t pos = loff_new[v] + (q - loff[v]);
+            int64_t pos = nb + (q - ob);
             const uint32_t c = fcount(f);
             if (c) pos += lower_bound_u32(fhub_new + fstart(f), c, hub_of(e));
             lent_new[pos] = e;
@@ -756,6 +791,8 @@ __global__ void k_finalize(const int64_t* loff, const uint32_t* lent, const int3
                            uint32_t* out_packed, uint32_t* out_hub, uint8_t* out_dist, int64_t n,
                            RoundCounters* ctr) {
     __shared__ int64_t sh_r[2];
+    __shared__ int64_t s_off[kMergeRows + 1];  // out_off of the tile's rows (as in k_merge_old)
+    __shared__ int64_t s_src[kMergeRows];      // start of each row in rank space
     const int64_t total = out_off[n];
     const int64_t ntiles = (total + kTileItems - 1) / kTileItems;
     uint32_t md = 0;
@@ -765,10 +802,28 @@ __global__ void k_finalize(const int64_t* loff, const uint32_t* lent, const int3
         if (threadIdx.x == 0) tile_rows(out_off, n, p0, p1, &sh_r[0], &sh_r[1]);
         __syncthreads();
         const int64_t r0 = sh_r[0], r1 = sh_r[1];
+        const int64_t rows = r1 - r0 + 1;
+        const int nr = rows <= kMergeRows ? (int)rows : kMergeRows + 1;
+        const bool staged = nr <= kMergeRows;
+        if (staged) {
+            for (int i = threadIdx.x; i <= nr; i += blockDim.x) s_off[i] = out_off[r0 + i];
+            for (int i = threadIdx.x; i < nr; i += blockDim.x) s_src[i] = loff[inv[r0 + i]];
+        }
+        __syncthreads();
         for (int64_t q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
-            const int64_t id = row_of(out_off, r0, r1, q);
-            const int32_t r = inv[id];
-            const uint32_t e = lent[loff[r] + (q - out_off[id])];
+            int64_t src;
+            if (staged) {
+                int lo = 0, hi = nr - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+                }
+                src = s_src[lo] + (q - s_off[lo]);
+            } else {
+                const int64_t id = row_of(out_off, r0, r1, q);
+                src = loff[inv[id]] + (q - out_off[id]);
+            }
+            const uint32_t e = lent[src];
             out_packed[q] = e;
             out_hub[q] = hub_of(e);
             out_dist[q] = (uint8_t)dist_of(e);
