@@ -486,7 +486,10 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         PLB_CK(launch_merge(cur, nxt));
         T = Tn;
         cur = nxt;
-        if (d == 1) {  // most rows reach kIndexMinLen in round 1: a packed rebuild
+        if (d == 1 || acc > T - acc) {
+            // most rows reach kIndexMinLen in round 1, and a round that more
+            // than doubles the labels outgrows most tables: a packed rebuild
+            // (cheaper than a new table per row from the shared pool cursor)
             const int e = build_index(cur, T);
             if (e != PLB_OK) return e;
         } else {

@@ -461,9 +461,10 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
                 PLB_ALLOC_OK();
             }
             PLB_CK(merge(S));
+            const int64_t Told = S.T;
             S.T = Tn;
             S.cur = x;
-            if (d == 1) {
+            if (d == 1 || Tn - Told > Told) {  // round 1, or a round that more than doubles the labels: repack
                 const int e = build_index(S);
                 if (e != PLB_OK) return e;
             } else {

@@ -537,13 +537,21 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
                                                                n, ctr);
             k_merge_new<<<grid_for((int64_t)n * 32, kFlatThreads, flat_grid_cap), kFlatThreads, 0, s>>>(
                 loff[cur], lent[cur], loff[x], lent[x], fse_new, store, A, ctr, top);
-            const int slots = index_slots(Tn);
-            k_index_update<<<flat_grid_cap, kIndexWarps * 32, sizeof(uint32_t) * kIndexWarps * slots, s>>>(
-                loff[x], lent[x], fse_new, store, A, htab, hdesc, (long long)hcap, slots, ctr);
-            launches += 7 + scan_n;
+            launches += 6 + scan_n;
             PLB_CK(cudaGetLastError());
+            const int64_t Told = T;
             T = Tn;
             cur = x;
+            if (acc > Told) {  // more than doubles the labels: most tables outgrown, repack
+                const int e = build_index();
+                if (e != PLB_OK) return e;
+            } else {
+                const int slots = index_slots(Tn);
+                k_index_update<<<flat_grid_cap, kIndexWarps * 32, sizeof(uint32_t) * kIndexWarps * slots, s>>>(
+                    loff[x], lent[x], fse_new, store, A, htab, hdesc, (long long)hcap, slots, ctr);
+                launches += 1;
+                PLB_CK(cudaGetLastError());
+            }
             base = (int64_t)hctr->cursor;  // this round's rows end here
             if (tm.on) tm.span(T_MERGE, m0, tm.mark());
         }
