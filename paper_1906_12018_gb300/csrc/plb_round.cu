@@ -673,9 +673,24 @@ __global__ void k_merge_new(const int64_t* loff, const uint32_t* lent, const int
         const uint32_t c = fcount(f);
         const uint32_t* fr = fhub_new + fstart(f);
         const int64_t ob = loff[v], ol = loff[v + 1] - ob;
-        for (uint32_t j = lane; j < c; j += 32) {
-            const uint32_t h = fr[j];
-            const int64_t pos = loff_new[v] + j + lower_bound_u32(lent + ob, ol, pack(h, 0));
+        // an old row of at most 32 entries sits in the lanes' registers: the
+        // old hubs below h are counted with shuffles instead of a binary
+        // search in global memory (c and ol are the same in every lane)
+        const bool reg = ol <= 32;
+        const uint32_t oe = reg && lane < ol ? lent[ob + lane] : 0xFFFFFFFFu;
+        for (uint32_t j0 = 0; j0 < c; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const uint32_t h = j < c ? fr[j] : 0u;
+            int64_t below;
+            if (reg) {
+                int cnt = 0;
+                for (int k = 0; k < (int)ol; ++k) cnt += __shfl_sync(kFull, oe, k) < pack(h, 0) ? 1 : 0;
+                below = cnt;
+            } else {
+                below = j < c ? lower_bound_u32(lent + ob, ol, pack(h, 0)) : 0;
+            }
+            if (j >= c) continue;
+            const int64_t pos = loff_new[v] + j + below;
             lent_new[pos] = pack(h, d);
             if (h < (uint32_t)kTopHubs && d <= (uint32_t)kTopLevels) {
                 uint32_t* tv = top + (int64_t)v * kTopRow + (h >> 5);
