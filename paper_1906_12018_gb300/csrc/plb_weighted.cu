@@ -286,7 +286,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     int64_t lcap[2] = {std::max<int64_t>(2 * n, 1024), std::max<int64_t>(2 * n, 1024)};
     int64_t* loff[2] = {pool.alloc<int64_t>(n + 1), pool.alloc<int64_t>(n + 1)};
     uint32_t* lent[2] = {pool.alloc<uint32_t>(lcap[0]), pool.alloc<uint32_t>(lcap[1])};
-    // frontier ring (S slots of n descriptors, then the empty one) and store
+    // frontier ring (S slots of 2^lgn descriptors, then the empty one) and store
     uint64_t* ring = pool.alloc<uint64_t>(ring_n + 1);
     int64_t scap = std::max<int64_t>(n + nnz + 1024, 4096);
     uint32_t* store = pool.alloc<uint32_t>(scap);
