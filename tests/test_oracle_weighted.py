@@ -215,3 +215,27 @@ def test_edge_weights_generator():
     assert all(back[(v, u)] == w for (u, v), w in back.items())      # both arcs of an edge alike
     assert np.array_equal(wt, G.edge_weights(g, 1, 7, 11))           # seeded
     assert not np.array_equal(wt, G.edge_weights(g, 1, 7, 12))
+
+
+def test_weighted_distance_overflow_is_reported():
+    """Label distances are uint8 up to 254: a path whose weighted length
+    passes 254 makes the oracle refuse (the GPU build reports
+    PLB_ERR_DIST_OVERFLOW for the same input), one just below does not."""
+    g, wt = wgraph(4, [(0, 1, 100), (1, 2, 100), (2, 3, 54)])
+    L = O.pll_weighted(g.off, g.col, wt, np.arange(4, dtype=np.int32))
+    assert L.max_dist == 254 and rows(L)[3] == [(0, 254), (1, 154), (2, 54), (3, 0)]
+    g, wt = wgraph(4, [(0, 1, 100), (1, 2, 100), (2, 3, 55)])
+    with pytest.raises(OverflowError):
+        O.pll_weighted(g.off, g.col, wt, np.arange(4, dtype=np.int32))
+
+
+def test_constant_weight_generator_and_labels():
+    g = G.rmat_graph(8, 4, 5)
+    wt = G.edge_weights(g, 3, 3, 1)
+    assert np.all(wt == 3)
+    order = G.degree_order(g)
+    W = O.pll_weighted(g.off, g.col, wt, order)
+    U = O.pll(g.off, g.col, order)
+    assert np.array_equal(W.hub, U.hub) and np.array_equal(W.dist.astype(np.int32), 3 * U.dist.astype(np.int32))
+    with pytest.raises(ValueError):
+        G.edge_weights(g, 0, 3, 1)
