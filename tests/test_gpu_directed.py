@@ -107,3 +107,26 @@ def test_directed_invalid_inputs():
         with pytest.raises(plb.PLBError) as e:                    # self-loop, unsorted row, out of range
             plb.build_directed(dev(o_, np.int64), dev(c_, np.int32), dev([0, 1, 2], np.int32))
         assert e.value.code == plb.PLB_ERR_INVALID
+
+
+def test_directed_bench_workload_sampled_rows():
+    """The directed bench workload (R-MAT arcs kept directed, 2^20 vertices,
+    edge factor 16, seed 3) with the default options: rows of sampled and of
+    the highest-degree vertices against Def. 2 in both directions, and
+    d(s -> t) against BFS from two sources."""
+    g = G.rmat_digraph(20, 16, 3)
+    order = G.directed_degree_order(g)
+    lin, lout = gpu_build_directed(g, order)
+    oi, hi, di = host_labels(lin)
+    oo, ho, do = host_labels(lout)
+    rng = np.random.default_rng(20)
+    deg = np.diff(g.off) + np.diff(g.off_in)
+    for v in list(rng.choice(g.n, 12, replace=False)) + list(np.argsort(-deg)[:3]):
+        h, d = O.chhl_row(g.off_in, g.col_in, order, int(v))
+        assert np.array_equal(hi[oi[v]:oi[v + 1]], h) and np.array_equal(di[oi[v]:oi[v + 1]], d), v
+        h, d = O.chhl_row(g.off, g.col, order, int(v))
+        assert np.array_equal(ho[oo[v]:oo[v + 1]], h) and np.array_equal(do[oo[v]:oo[v + 1]], d), v
+    for s in rng.choice(g.n, 2, replace=False):
+        p = np.stack([np.full(g.n, s), np.arange(g.n)], 1).astype(np.int32)
+        got = plb.query_directed(lout, lin, dev(p, np.int32)).cpu().numpy()
+        assert np.array_equal(got, O.bfs(g.off, g.col, int(s)))
