@@ -169,9 +169,16 @@ def max_over_ranks(x: float, world: int) -> float:
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Units per second of the whole job: every rank processes the same
+    workload (replicas), timed by the slowest rank."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 def oracle_total_labels(name: str) -> int | None:
@@ -699,7 +706,7 @@ def main():
             cpu = pll_sample(g, order, total, args.cpu_seconds)
 
     if rank == 0:
-        value = g.m * world / (ms_max / 1e3)
+        value = whole_job_rate(g.m, ms_max, world)
         line = {
             "metric": "labeling edges/sec",
             "value": value,
@@ -730,7 +737,7 @@ def main():
                           "finalize": st["ms_finalize"]},
             "counters": {k: st[k] for k in ("receivers", "messages_round", "unique_round", "prefiltered_round",
                                             "probed_round", "accepted", "tier_vertices", "launches")},
-            "e2e": {"value": g.m * world / (e2e_ms_med / 1e3), "unit": "edges/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": whole_job_rate(g.m, e2e_ms_med, world), "unit": "edges/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_med},
             "queries": {"value": q_value, "unit": "queries/s", "batch": 1 << 16,
                         "p50_ms": qms[len(qms) // 2], "p99_ms": qms[min(len(qms) - 1, int(0.99 * len(qms)))]},

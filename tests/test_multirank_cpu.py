@@ -1,0 +1,68 @@
+"""The benchmark's multi-rank host logic on CPU: two gloo ranks (one process
+each) meet at the barrier, take the slowest rank's time and report the
+whole-job rate; a non-zero rank of the reference arm exits without work."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank: int, world: int, port: int, q) -> None:
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        bench.barrier(world)
+        ms = bench.max_over_ranks(10.0 + rank, world)  # rank 1 is the slowest
+        q.put((rank, ms, bench.whole_job_rate(1000.0, ms, world)))
+        bench.barrier(world)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_report_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(60)
+    assert [p.exitcode for p in procs] == [0, 0]
+    assert [r for r, _, _ in got] == [0, 1]
+    for _, ms, rate in got:
+        assert ms == 11.0                                 # max over ranks
+        assert rate == pytest.approx(2 * 1000.0 / 0.011)  # both ranks' units over the slowest time
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    bench.barrier(1)
+    assert bench.whole_job_rate(500.0, 250.0, 1) == pytest.approx(2000.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    import argparse
+
+    import bench
+
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    args = argparse.Namespace(workload="rmat12", steps=1, warmup=0, ref_seconds=0.1)
+    assert bench.run_reference(args) == 0  # returns before any work
