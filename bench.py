@@ -241,6 +241,46 @@ def run_reference(args):
     return 0
 
 
+def _oracle_small_graph(i: int):
+    """Worker: the oracle's PLL (Alg. 1) on graph i of the batched workload;
+    (edges, labels, seconds of the labeling alone)."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import oracle as O
+    from paper_1906_12018_gb300 import graphs as G
+
+    g = G.small_graph(i)
+    order = G.degree_order(g)
+    t = time.perf_counter()
+    lab = O.pll(g.off, g.col, order)
+    return g.m, lab.total, time.perf_counter() - t
+
+
+def oracle_batch_sample(seconds: float, cores: int, limit: int = 2000) -> dict:
+    """The oracle on a bounded sample of the batched workload: graphs 0, 1, ...
+    labeled one after another on one core until `seconds` have passed, then
+    the same graphs as independent jobs over `cores` processes (started with
+    spawn: the caller may hold a CUDA context).  Edges per second of each."""
+    import multiprocessing as mproc
+
+    done, edges, t1 = 0, 0, 0.0
+    while done < limit and t1 < seconds:
+        m, _, el = _oracle_small_graph(done)
+        edges += m
+        t1 += el
+        done += 1
+    with mproc.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_small_graph, range(min(cores, done)))  # start the workers
+        t = time.perf_counter()
+        pool.map(_oracle_small_graph, range(done), chunksize=1)
+        tall = time.perf_counter() - t
+    return {"value": edges / t1, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"PLL (Alg. 1) on graphs 0..{done - 1} of the batch ({edges} edges, {t1:.1f} s on one core)",
+            "all_cores": {"value": edges / tall, "unit": "edges/s", "cores": cores,
+                          "sample": f"the same {done} graphs as independent jobs ({tall:.1f} s wall, graph "
+                                    "generation inside the jobs)"}}
+
+
 def run_batch(args):
     """2,000 small graphs (sizes log-uniform 1k-64k; half R-MAT edge factor 8,
     half Chung-Lu gamma 2.3 mean degree 10; seeds 100-2099): one plb_build
@@ -283,6 +323,9 @@ def run_batch(args):
     t_loop = min(timed(loop) for _ in range(2))
     t_def = min(timed(batch(None)) for _ in range(max(args.steps, 1)))  # the batch API's defaults
     t_tuned = min(timed(batch(tuned)) for _ in range(max(args.steps, 1)))
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_batch_sample(args.cpu_seconds, os.cpu_count() or 1, k)
     line = {"metric": "labeling edges/sec", "value": m / t_tuned, "unit": "edges/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tuned, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -290,7 +333,7 @@ def run_batch(args):
             "one_graph_at_a_time": {"value": m / t_loop, "ms": 1e3 * t_loop},
             "batched_default": {"value": m / t_def, "ms": 1e3 * t_def},
             "batched_tuned": {"value": m / t_tuned, "ms": 1e3 * t_tuned, "options": autotune.as_dict(tuned)},
-            "speedup_vs_one_at_a_time": t_loop / t_tuned, "autotune": tune_report}
+            "speedup_vs_one_at_a_time": t_loop / t_tuned, "autotune": tune_report, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -1,6 +1,7 @@
-"""The benchmark's multi-rank host logic on CPU: two gloo ranks (one process
-each) meet at the barrier, take the slowest rank's time and report the
-whole-job rate; a non-zero rank of the reference arm exits without work."""
+"""The benchmark's host logic on CPU: two gloo ranks (one process each) meet
+at the barrier, take the slowest rank's time and report the whole-job rate;
+a non-zero rank of the reference arm exits without work; the batched
+workload's oracle baseline (one core, then a spawn-started pool)."""
 import os
 import socket
 
@@ -66,3 +67,14 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = argparse.Namespace(workload="rmat12", steps=1, warmup=0, ref_seconds=0.1)
     assert bench.run_reference(args) == 0  # returns before any work
+
+
+def test_oracle_batch_sample_single_and_all_cores():
+    """The batched workload's CPU baseline: one core, then the same graphs
+    over a spawn-started process pool; both count the same edges."""
+    import bench
+
+    r = bench.oracle_batch_sample(0.05, 2, limit=3)
+    n = int(r["sample"].split("graphs 0..")[1].split(" ")[0]) + 1
+    assert 1 <= n <= 3 and r["cores"] == 1 and r["all_cores"]["cores"] == 2
+    assert r["value"] > 0 and r["all_cores"]["value"] > 0
