@@ -85,6 +85,8 @@ def _load():
     lib.oracle_labels_stats.restype = ctypes.POINTER(ctypes.c_int64)
     lib.oracle_labels_export.argtypes = [P, P, P, P]
     lib.oracle_labels_export.restype = None
+    lib.oracle_labels_cost.argtypes = [P, P]
+    lib.oracle_labels_cost.restype = None
     lib.oracle_query.argtypes = [I64, P, P, P, P, P]
     lib.oracle_query.restype = None
     lib.oracle_bfs.argtypes = [I64, P, P, ctypes.c_int32, P]
@@ -119,6 +121,7 @@ class Labels:
     max_dist: int = 0
     rounds: int = 0
     round_stats: np.ndarray | None = None  # VC-PLL: [round, (messages, unique, accepted, checks)]
+    cost: np.ndarray | None = None  # PLL / VC-PLL: per vertex, positive distance-check cost (Sec. 4.3)
 
     @property
     def n(self) -> int:
@@ -155,8 +158,10 @@ def _export(h, n) -> Labels:
     rounds = lib.oracle_labels_rounds(h)
     st = lib.oracle_labels_stats(h)
     stats = np.ctypeslib.as_array(st, shape=(256, 4)).copy() if rounds else None
+    cost = np.zeros(max(n, 1), dtype=np.int64)
+    lib.oracle_labels_cost(h, _p(cost))
     lab = Labels(off, hub[:total].copy(), dist[:total].copy(), lib.oracle_labels_max_dist(h),
-                 rounds, stats)
+                 rounds, stats, cost[:n])
     lib.oracle_labels_free(h)
     return lab
 

@@ -66,6 +66,7 @@ typedef struct {
     int32_t max_dist;
     int32_t rounds;          /* VC-PLL only */
     int64_t stats[4 * 256];  /* VC-PLL per round: messages, unique, accepted, checks */
+    int64_t* cost;           /* per vertex: positive distance-check cost (Sec. 4.3), PLL and VC-PLL */
 } labels_t;
 
 static int row_push(row_t* r, uint32_t h, uint8_t d) {
@@ -89,6 +90,7 @@ static labels_t* labels_new(int64_t n) {
     labels_t* L = (labels_t*)calloc(1, sizeof(labels_t));
     L->n = n;
     L->rows = (row_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(row_t));
+    L->cost = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
     return L;
 }
 
@@ -100,6 +102,7 @@ void oracle_labels_free(void* h) {
         free(L->rows[v].dist);
     }
     free(L->rows);
+    free(L->cost);
     free(L);
 }
 
@@ -107,6 +110,16 @@ int64_t oracle_labels_total(void* h) { return ((labels_t*)h)->total; }
 int32_t oracle_labels_max_dist(void* h) { return ((labels_t*)h)->max_dist; }
 int32_t oracle_labels_rounds(void* h) { return ((labels_t*)h)->rounds; }
 const int64_t* oracle_labels_stats(void* h) { return ((labels_t*)h)->stats; }
+
+/* Positive distance-check cost per vertex (Sec. 4.3, the positive-check
+ * theorem): over the labels (u, d) accepted at v, u != v, the number of v's
+ * other labels (v's own (v, 0) left out) that the check of (u, d) reads.
+ * PLL (Alg. 1) reads every label accepted before (roots arrive one by one);
+ * VC-PLL (Alg. 3) reads the labels of the earlier rounds only. */
+void oracle_labels_cost(void* h, int64_t* out) {
+    labels_t* L = (labels_t*)h;
+    memcpy(out, L->cost, sizeof(int64_t) * (size_t)L->n);
+}
 
 /* CSR export: off[n+1], hub[total], dist[total], rows by original id. */
 void oracle_labels_export(void* h, int64_t* off, uint32_t* hub, uint8_t* dist) {
@@ -189,6 +202,7 @@ static void* pll_impl(int64_t n, const int64_t* off, const int32_t* col, const i
                 fail = 1;
                 break;
             }
+            if (v != u) L->cost[v] += L->rows[v].len;    /* L(v) holds no (v, 0) yet: v ranks below u */
             if (row_push(&L->rows[v], (uint32_t)r, (uint8_t)delta)) {
                 fail = 1;
                 break;
@@ -374,7 +388,10 @@ void* oracle_vcpll(int64_t n, const int64_t* off, const int32_t* col, const int3
                         break;
                     }
                 }
-                if (!pruned) row_push(&ndL[v], u, (uint8_t)(d > 255 ? 255 : d));
+                if (!pruned) {
+                    row_push(&ndL[v], u, (uint8_t)(d > 255 ? 255 : d));
+                    L->cost[v] += Lv->len - 1;                /* the labels of rounds < d, (v, 0) left out */
+                }
             }
             for (int64_t i = 0; i < Lv->len; ++i) Tv[Lv->hub[i]] = INF_D;
             for (int64_t k = 0; k < nm; ++k) seen[msgs[k]] = -1;
