@@ -280,3 +280,15 @@ def test_chhl_row_matches_full(rmat12):
         h, d = O.chhl_row(g.off, g.col, order, v)
         fh, fd = full.row(v)
         assert np.array_equal(h, fh) and np.array_equal(d, fd)
+
+
+@pytest.mark.parametrize("i", [12, 18, 19, 25])
+def test_batch_workload_graphs_match_definition(i):
+    """Graphs of the batched workload (even i: R-MAT + LCC; odd i: Chung-Lu
+    with isolated vertices): Alg. 1 and Alg. 3 equal Def. 2 computed by
+    brute force, one BFS per vertex."""
+    g = G.small_graph(i)
+    order = G.degree_order(g)
+    ref = O.chhl(g.off, g.col, order)
+    for L in (O.pll(g.off, g.col, order), O.vcpll(g.off, g.col, order)):
+        assert np.array_equal(L.off, ref.off) and np.array_equal(L.hub, ref.hub) and np.array_equal(L.dist, ref.dist)
