@@ -181,6 +181,32 @@ def whole_job_rate(units_per_rank: float, ms_max: float, world: int) -> float:
     return units_per_rank * world / (ms_max / 1e3)
 
 
+def host_cpu() -> dict:
+    """The host the CPU baselines ran on: architecture, logical cores and CPU
+    model (lscpu, else /proc/cpuinfo)."""
+    import platform
+
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part", "hardware")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"machine": platform.machine(), "nproc": os.cpu_count(), "model": model}
+
+
 def oracle_total_labels(name: str) -> int | None:
     """Canonical label total of a named workload, as written by
     oracle/workload_totals.py (a full oracle PLL run)."""
@@ -202,7 +228,7 @@ def pll_sample(g, order, total: int, seconds: float) -> dict:
     lab, roots, el = O.pll_budget(g.off, g.col, order, seconds)
     frac = lab.total / max(total, 1)
     est = el / max(frac, 1e-12)
-    return {"value": g.m / est, "unit": "edges/s", "cores": 1, "kind": "oracle",
+    return {"value": g.m / est, "unit": "edges/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": (f"PLL (Alg. 1) over the first {roots} roots in rank order ({el:.1f} s, "
                        f"{lab.total} of {total} labels = {100 * frac:.1f}%); time scaled by label share"),
             "sample_seconds": el}
@@ -234,7 +260,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1000 * sec, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "n": g.n, "m": g.m}, "impl": "reference",
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "edges/s",
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "edges/s", "host": host_cpu(),
                              "sample": samples[0]["sample"]},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -274,7 +300,7 @@ def oracle_batch_sample(seconds: float, cores: int, limit: int = 2000) -> dict:
         t = time.perf_counter()
         pool.map(_oracle_small_graph, range(done), chunksize=1)
         tall = time.perf_counter() - t
-    return {"value": edges / t1, "unit": "edges/s", "cores": 1, "kind": "oracle",
+    return {"value": edges / t1, "unit": "edges/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"PLL (Alg. 1) on graphs 0..{done - 1} of the batch ({edges} edges, {t1:.1f} s on one core)",
             "all_cores": {"value": edges / tall, "unit": "edges/s", "cores": cores,
                           "sample": f"the same {done} graphs as independent jobs ({tall:.1f} s wall, graph "
@@ -431,6 +457,7 @@ def run_weighted(args):
         part, roots, el = O.pll_weighted_budget(g.off, g.col, wt, order, args.cpu_seconds)
         frac = part.total / max(total, 1)
         cpu = {"value": g.m / (el / max(frac, 1e-12)), "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "host": host_cpu(),
                "sample": (f"PLL with pruned Dijkstra searches over the first {roots} roots in rank order "
                           f"({el:.1f} s, {part.total} of {total} labels = {100 * frac:.1f}%); time scaled by "
                           "label share")}

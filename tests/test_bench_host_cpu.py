@@ -78,3 +78,10 @@ def test_oracle_batch_sample_single_and_all_cores():
     n = int(r["sample"].split("graphs 0..")[1].split(" ")[0]) + 1
     assert 1 <= n <= 3 and r["cores"] == 1 and r["all_cores"]["cores"] == 2
     assert r["value"] > 0 and r["all_cores"]["value"] > 0
+
+
+def test_host_cpu_is_recorded():
+    import bench
+
+    h = bench.host_cpu()
+    assert h["nproc"] == os.cpu_count() and h["machine"] and isinstance(h["model"], str)
