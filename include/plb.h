@@ -10,6 +10,10 @@
  *   - construction: Alg. 3 (VC-PLL, Sec. 3.1), one vertex-centric round per
  *     distance d = 1, 2, ...; Thm. 1 shows it yields the labels of Def. 2.
  *   - query: Sec. 2.1, Dis(u,v) = min over common hubs h of d(u,h)+d(h,v).
+ *   - variants (Sec. 5.1): directed graphs (plb_build_directed: L_in and
+ *     L_out in the same rounds) and weighted graphs (plb_build_weighted:
+ *     rounds by distance value); rank batches of Alg. 4 (plb_options.
+ *     batch_hubs); many graphs in one round loop (plb_build_batch).
  *
  * General conventions
  *   - Every pointer argument that names graph, order, pair or distance data
@@ -17,8 +21,8 @@
  *     its comment says "host".  Inputs are read-only for the duration of the
  *     call and stay owned by the caller.
  *   - Calls are ordered on the given stream (NULL = the legacy default
- *     stream).  plb_build / plb_build_batch synchronise the stream internally
- *     (one device->host read per round); plb_query_batch and
+ *     stream).  The builds synchronise the stream internally (one or two
+ *     device->host reads per round); plb_query_batch and
  *     plb_degree_order are asynchronous: results are ready when the stream is.
  *   - Vertices are int32 ids 0..n-1.  "rank" r in 0..n-1 is the position in
  *     the vertex order (rank 0 = highest); order[r] = id of rank r.
@@ -47,7 +51,7 @@ enum plb_status {
     PLB_ERR_DIST_OVERFLOW = 3,  /* a label distance would exceed 254 */
     PLB_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired */
     PLB_ERR_CUDA = 5,           /* a CUDA runtime call or launch failed */
-    PLB_ERR_TOO_LARGE = 6       /* n >= 2^24 */
+    PLB_ERR_TOO_LARGE = 6       /* n >= 2^24 (or a weighted build's frontier ring too large) */
 };
 
 #define PLB_MAX_VERTICES (1 << 24)
