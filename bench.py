@@ -52,16 +52,32 @@ def gather_prune_bytes(st: dict, n: int) -> int:
 # profiles/ (valid only while the kernel sources hash to the recorded value).
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "gp_traffic_chunglu20.md")
 KERNEL_SOURCES = ("paper_1906_12018_gb300/csrc/plb_gather.cu", "paper_1906_12018_gb300/csrc/plb_kernels.cuh",
-                  "paper_1906_12018_gb300/csrc/plb_internal.cuh", "paper_1906_12018_gb300/csrc/plb_round.cu")
+                  "paper_1906_12018_gb300/csrc/plb_internal.cuh")
+# the round-1 kernels (k_round1_count, k_round1): their section of plb_round.cu
+ROUND1_SECTION = ("paper_1906_12018_gb300/csrc/plb_round.cu", "// Both passes run flat over tiles of arcs",
+                  "// Reset before re-running the gather/prune")
+
+
+def round1_section() -> str:
+    """Source of the round-1 kernels and of the file-local helpers ahead of
+    them (the whole file when a marker is gone)."""
+    rel, a, b = ROUND1_SECTION
+    with open(os.path.join(ROOT, rel)) as f:
+        text = f.read()
+    i, j, k = text.find(a), text.find(b), text.find("}  // namespace")
+    return text[:k] + text[i:j] if 0 <= k < i < j else text
 
 
 def kernel_source_hash() -> str:
+    """SHA-256 over the sources of the gather + prune class: the gather
+    kernels' files and the round-1 kernels' section."""
     import hashlib
 
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
+    h.update(round1_section().encode())
     return h.hexdigest()
 
 

@@ -85,3 +85,13 @@ def test_host_cpu_is_recorded():
 
     h = bench.host_cpu()
     assert h["nproc"] == os.cpu_count() and h["machine"] and isinstance(h["model"], str)
+
+
+def test_traffic_guard_covers_the_round1_kernels():
+    """The traffic record's hash covers the round-1 kernels' source (found by
+    its markers), not the rest of their file."""
+    import bench
+
+    sec = bench.round1_section()
+    assert "k_round1_count" in sec and "k_round1(" in sec and "tile_rows" in sec
+    assert "k_merge_new" not in sec and "k_index_build" not in sec
