@@ -25,10 +25,15 @@ Functions (each restates one definition or algorithm of the paper, Jin et al.,
 * ``dijkstra``  textbook Dijkstra distances
 
 Labels come back as ``Labels(off, hub, dist)``: rows indexed by original id,
-hub = rank (uint32), dist uint8, each row sorted by hub rank.
+hub = rank (uint32), dist uint8, each row sorted by hub rank.  ``pll`` and
+``vcpll`` also count, per vertex, the positive distance-check cost of Sec. 4.3
+(``Labels.cost``: over the labels accepted at v, the other labels of v that
+each check reads).
 
-Pinning: see ``tests/test_oracle.py`` (scipy all-pairs distances and the
-shortest-path-set form of Def. 2, closed forms, invariants, paper identities).
+Pinning: ``tests/test_oracle.py`` (scipy all-pairs distances and the
+shortest-path-set form of Def. 2, closed forms, invariants, paper identities),
+``tests/test_oracle_directed.py``, ``tests/test_oracle_weighted.py``,
+``tests/test_oracle_cost.py``.
 """
 from __future__ import annotations
 
