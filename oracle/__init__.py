@@ -9,6 +9,8 @@ Functions (each restates one definition or algorithm of the paper, Jin et al.,
 
 * ``pll``       Alg. 1, sequential pruned BFS per root in rank order (Sec. 2.1.1)
 * ``vcpll``     Alg. 3, vertex-centric rounds with unique messages (Sec. 3.1)
+* ``bvcpll``    Alg. 4 (BVC-PLL, Sec. 4.2): hubs in rank batches, a candidate
+                bit-vector per vertex and batch, vertex-centric rounds
 * ``chhl``      Def. 2, canonical labels by definition (one BFS per vertex)
 * ``chhl_row``  Def. 2 for a single vertex (usable on large graphs)
 * ``query``     2-hop distance query (Sec. 2.1)
@@ -92,6 +94,10 @@ def _load():
     lib.oracle_labels_export.restype = None
     lib.oracle_labels_cost.argtypes = [P, P]
     lib.oracle_labels_cost.restype = None
+    lib.oracle_labels_checks.argtypes = [P]
+    lib.oracle_labels_checks.restype = I64
+    lib.oracle_bvcpll.argtypes = [I64, P, P, P, I64]
+    lib.oracle_bvcpll.restype = P
     lib.oracle_query.argtypes = [I64, P, P, P, P, P]
     lib.oracle_query.restype = None
     lib.oracle_bfs.argtypes = [I64, P, P, ctypes.c_int32, P]
@@ -127,6 +133,7 @@ class Labels:
     rounds: int = 0
     round_stats: np.ndarray | None = None  # VC-PLL: [round, (messages, unique, accepted, checks)]
     cost: np.ndarray | None = None  # PLL / VC-PLL: per vertex, positive distance-check cost (Sec. 4.3)
+    checks: int = 0  # PLL: vertices reached over all pruned searches; BVC-PLL: messages sent
 
     @property
     def n(self) -> int:
@@ -166,7 +173,7 @@ def _export(h, n) -> Labels:
     cost = np.zeros(max(n, 1), dtype=np.int64)
     lib.oracle_labels_cost(h, _p(cost))
     lab = Labels(off, hub[:total].copy(), dist[:total].copy(), lib.oracle_labels_max_dist(h),
-                 rounds, stats, cost[:n])
+                 rounds, stats, cost[:n], int(lib.oracle_labels_checks(h)))
     lib.oracle_labels_free(h)
     return lab
 
@@ -203,6 +210,16 @@ def pll_budget(off, col, order, seconds: float):
 def vcpll(off, col, order) -> Labels:
     """Alg. 3 (VC-PLL), with per-round message / unique / accepted / check counts."""
     return _run("oracle_vcpll", off, col, order)
+
+
+def bvcpll(off, col, order, batch: int) -> Labels:
+    """Alg. 4 (BVC-PLL) with hub batches of ``batch`` consecutive ranks;
+    ``checks`` counts the messages sent (one distance check each)."""
+    n, off, col, order = _csr_args(off, col, order)
+    h = _load().oracle_bvcpll(n, _p(off), _p(col), _p(order), int(batch))
+    if not h:
+        raise OverflowError("label distance above 254 (or out of memory)")
+    return _export(h, n)
 
 
 def chhl(off, col, order) -> Labels:

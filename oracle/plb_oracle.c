@@ -67,6 +67,7 @@ typedef struct {
     int32_t rounds;          /* VC-PLL only */
     int64_t stats[4 * 256];  /* VC-PLL per round: messages, unique, accepted, checks */
     int64_t* cost;           /* per vertex: positive distance-check cost (Sec. 4.3), PLL and VC-PLL */
+    int64_t checks;          /* PLL: vertices reached (popped) over all searches; BVC-PLL: messages sent */
 } labels_t;
 
 static int row_push(row_t* r, uint32_t h, uint8_t d) {
@@ -107,6 +108,7 @@ void oracle_labels_free(void* h) {
 }
 
 int64_t oracle_labels_total(void* h) { return ((labels_t*)h)->total; }
+int64_t oracle_labels_checks(void* h) { return ((labels_t*)h)->checks; }
 int32_t oracle_labels_max_dist(void* h) { return ((labels_t*)h)->max_dist; }
 int32_t oracle_labels_rounds(void* h) { return ((labels_t*)h)->rounds; }
 const int64_t* oracle_labels_stats(void* h) { return ((labels_t*)h)->stats; }
@@ -187,6 +189,7 @@ static void* pll_impl(int64_t n, const int64_t* off, const int32_t* col, const i
         while (head < tail) {
             const int32_t v = Q[head++];
             const int32_t delta = D[v];
+            ++L->checks;                                 /* one distance check per reached vertex */
             /* prune iff some common hub w gives T[w] + d(w,v) <= delta */
             int pruned = 0;
             const row_t* Lv = &L->rows[v];
@@ -862,6 +865,135 @@ void* oracle_chhl_weighted(int64_t n, const int64_t* off, const int32_t* col, co
         for (int64_t i = 0; i < k; ++i) row_push(&L->rows[v], hh[i], dd[i]);
     }
     free(rank); free(dist); free(best); free(settled); free(done); free(hh); free(dd); free(hp.key);
+    finish_totals(L);
+    return L;
+}
+
+/* ----------------------------------------------------------------- Alg. 4 */
+/* BVC-PLL: hubs in batches of B consecutive ranks.  Per batch: the batch's
+ * vertices start with dL(u) = {(u, 0)} added to L(u); then vertex-centric
+ * rounds: every active a sends each (u, d) of dL(a) to each neighbour v with
+ * rank(u) < rank(v) whose candidate bit-vector C(v) does not hold u yet (the
+ * bit is set: u reaches v at most once per batch); each v that received
+ * messages accepts (u, d) iff d < min over common hubs h of L(u) and L(v) of
+ * d(u,h) + d(h,v), with the labels as they stood after the previous round;
+ * the accepted ones form dL(v), are added to L(v) and make v active.  C is
+ * cleared after the batch.  checks = messages sent.  NULL on a distance
+ * above 254 or allocation failure. */
+static int32_t row_find(const row_t* r, uint32_t hub) {   /* distance of hub in a rank-sorted row, or -1 */
+    int64_t lo = 0, hi = r->len;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (r->hub[mid] < hub) lo = mid + 1; else hi = mid;
+    }
+    return lo < r->len && r->hub[lo] == hub ? (int32_t)r->dist[lo] : -1;
+}
+
+static int row_insert_sorted(row_t* r, uint32_t hub, uint8_t d) {
+    if (row_push(r, hub, d)) return -1;
+    int64_t p = r->len - 1;
+    while (p > 0 && r->hub[p - 1] > r->hub[p]) {
+        uint32_t th = r->hub[p]; r->hub[p] = r->hub[p - 1]; r->hub[p - 1] = th;
+        uint8_t td = r->dist[p]; r->dist[p] = r->dist[p - 1]; r->dist[p - 1] = td;
+        --p;
+    }
+    return 0;
+}
+
+void* oracle_bvcpll(int64_t n, const int64_t* off, const int32_t* col, const int32_t* order, int64_t B) {
+    labels_t* L = labels_new(n);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    if (B < 1) B = 1;
+    int32_t* rank = (int32_t*)malloc(sizeof(int32_t) * nn);
+    row_t* dL = (row_t*)calloc(nn, sizeof(row_t));       /* dL(a): (hub rank, distance) of the last round */
+    row_t* msg = (row_t*)calloc(nn, sizeof(row_t));      /* v.messages */
+    row_t* ndL = (row_t*)calloc(nn, sizeof(row_t));
+    unsigned char* C = (unsigned char*)calloc(nn * (size_t)(B < n ? B : (n > 0 ? n : 1)), 1);  /* C(v), B bits as bytes */
+    int32_t* active = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* next = (int32_t*)malloc(sizeof(int32_t) * nn);
+    int32_t* recv = (int32_t*)malloc(sizeof(int32_t) * nn);
+    const int64_t Bw = B < n ? B : (n > 0 ? n : 1);
+    int fail = 0;
+    for (int64_t r = 0; r < n; ++r) rank[order[r]] = (int32_t)r;
+    for (int64_t lo = 0; lo < n && !fail; lo += B) {
+        const int64_t hi = lo + B < n ? lo + B : n;
+        int64_t na = 0;
+        for (int64_t r = lo; r < hi; ++r) {                /* the batch's vertices: dL(u) = {(u, 0)} */
+            const int32_t u = order[r];
+            dL[u].len = 0;
+            if (row_push(&dL[u], (uint32_t)r, 0) || row_insert_sorted(&L->rows[u], (uint32_t)r, 0)) fail = 1;
+            active[na++] = u;
+        }
+        int32_t d = 0;
+        while (na > 0 && !fail) {
+            ++d;
+            int64_t nr = 0;
+            for (int64_t i = 0; i < na; ++i) {             /* scatter */
+                const int32_t a = active[i];
+                for (int64_t j = off[a]; j < off[a + 1]; ++j) {
+                    const int32_t v = col[j];
+                    for (int64_t k = 0; k < dL[a].len; ++k) {
+                        const uint32_t u = dL[a].hub[k];
+                        unsigned char* bit = &C[(size_t)v * (size_t)Bw + (size_t)((int64_t)u - lo)];
+                        if ((int64_t)u < (int64_t)rank[v] && !*bit) {
+                            *bit = 1;
+                            if (msg[v].len == 0) recv[nr++] = v;
+                            if (row_push(&msg[v], u, (uint8_t)(dL[a].dist[k] + 1 > 255 ? 255 : dL[a].dist[k] + 1)))
+                                fail = 1;
+                            ++L->checks;
+                        }
+                    }
+                }
+            }
+            for (int64_t i = 0; i < na; ++i) dL[active[i]].len = 0;
+            for (int64_t i = 0; i < nr; ++i) {             /* gather (labels of the previous rounds) */
+                const int32_t v = recv[i];
+                const row_t* Lv = &L->rows[v];
+                ndL[v].len = 0;
+                for (int64_t k = 0; k < msg[v].len; ++k) {
+                    const uint32_t u = msg[v].hub[k];
+                    const int32_t duv = msg[v].dist[k];
+                    const row_t* Lu = &L->rows[order[u]];
+                    int pruned = 0;
+                    for (int64_t e = 0; e < Lv->len && !pruned; ++e) {
+                        const int32_t du = row_find(Lu, Lv->hub[e]);
+                        if (du >= 0 && du + (int32_t)Lv->dist[e] <= duv) pruned = 1;
+                    }
+                    if (!pruned) {
+                        if (duv > 254) fail = 1;
+                        else if (row_push(&ndL[v], u, (uint8_t)duv)) fail = 1;
+                    }
+                }
+                msg[v].len = 0;
+            }
+            int64_t nn2 = 0;
+            for (int64_t i = 0; i < nr; ++i) {             /* L(v) <- L(v) U dL(v); v becomes active */
+                const int32_t v = recv[i];
+                if (ndL[v].len == 0) continue;
+                for (int64_t k = 0; k < ndL[v].len; ++k)
+                    if (row_insert_sorted(&L->rows[v], ndL[v].hub[k], ndL[v].dist[k])) fail = 1;
+                row_t t = dL[v];
+                dL[v] = ndL[v];
+                ndL[v] = t;
+                ndL[v].len = 0;
+                next[nn2++] = v;
+            }
+            for (int64_t i = 0; i < nn2; ++i) active[i] = next[i];
+            na = nn2;
+        }
+        for (int64_t i = 0; i < na; ++i) dL[active[i]].len = 0;
+        memset(C, 0, nn * (size_t)Bw);                     /* C(v) <- empty after the batch */
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        free(dL[v].hub); free(dL[v].dist);
+        free(msg[v].hub); free(msg[v].dist);
+        free(ndL[v].hub); free(ndL[v].dist);
+    }
+    free(dL); free(msg); free(ndL); free(C); free(active); free(next); free(recv); free(rank);
+    if (fail) {
+        oracle_labels_free(L);
+        return NULL;
+    }
     finish_totals(L);
     return L;
 }
