@@ -67,3 +67,32 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(plb.Options) == 16 * 4
     assert ctypes.sizeof(plb.CSR) == 32
     assert ctypes.sizeof(plb.LabelView) == 6 * 8 + 8
+
+
+def test_variant_entry_points_reject_bad_arguments_before_device_work(lib):
+    from paper_1906_12018_gb300 import plb
+
+    lib = plb._lib()
+    h, h2 = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.plb_build_directed(None, None, None, None, ctypes.byref(h), ctypes.byref(h2)) == plb.PLB_ERR_INVALID
+    assert lib.plb_build_weighted(None, None, None, None, None, ctypes.byref(h)) == plb.PLB_ERR_INVALID
+    g = plb.CSR(4, 2, 1, 1)                      # arcs but no weight array
+    assert lib.plb_build_weighted(ctypes.byref(g), None, 1, None, None, ctypes.byref(h)) == plb.PLB_ERR_INVALID
+    big = plb.CSR(1 << 24, 0, 1, None)
+    assert lib.plb_build_weighted(ctypes.byref(big), None, 1, None, None, ctypes.byref(h)) == plb.PLB_ERR_TOO_LARGE
+    o = plb.default_options()
+    assert o.warp_stage_ratio == 4 and o.batch_hubs == 0
+    bad = plb.default_options(warp_stage_ratio=2000)   # outside 0..1024: refused with the options check
+    assert lib.plb_build(ctypes.byref(g), 1, ctypes.byref(bad), None, ctypes.byref(h)) == plb.PLB_ERR_INVALID
+
+
+def test_binding_refuses_host_tensors():
+    torch = pytest.importorskip("torch")
+    from paper_1906_12018_gb300 import plb
+
+    off = torch.zeros(2, dtype=torch.int64)
+    col = torch.zeros(0, dtype=torch.int32)
+    with pytest.raises(TypeError):
+        plb.build_weighted(off, col, torch.zeros(0, dtype=torch.uint8), torch.zeros(1, dtype=torch.int32))
+    with pytest.raises(TypeError):
+        plb.build_directed(off, col, torch.zeros(1, dtype=torch.int32))
