@@ -1,6 +1,7 @@
 // Host-side helpers of the build drivers (undirected: plb_build.cu;
-// directed: plb_directed.cu): device allocations of one build, CUDA-event
-// timers, launch geometry, the last CUDA error of this thread.
+// directed: plb_directed.cu; weighted: plb_weighted.cu): device allocations
+// of one build, CUDA-event timers, launch geometry, the last CUDA error of
+// this thread.
 #pragma once
 
 #include <algorithm>
