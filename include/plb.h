@@ -49,7 +49,9 @@ enum plb_status {
     PLB_ERR_INVALID = 1,        /* bad argument, bad CSR, order not a permutation */
     PLB_ERR_OOM = 2,            /* device allocation failed */
     PLB_ERR_DIST_OVERFLOW = 3,  /* a label distance would exceed 254 */
-    PLB_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired */
+    PLB_ERR_TIMEOUT = 4,        /* reserved for a bounded device-side wait that expired: no
+                                 * kernel of this library waits on another (graph-mode round
+                                 * loops end by the round limit), so no call returns it now */
     PLB_ERR_CUDA = 5,           /* a CUDA runtime call or launch failed */
     PLB_ERR_TOO_LARGE = 6       /* n >= 2^24 (or a weighted build's frontier ring too large) */
 };

@@ -296,10 +296,14 @@ class Labels:
     def query(self, pairs: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """pairs: CUDA int32 [q, 2] (original ids) -> CUDA int32 [q] distances."""
         pairs = _dev(pairs.reshape(-1), torch.int32, "pairs")
+        if pairs.numel() % 2:
+            raise ValueError("pairs must hold an even number of ids (s, t)")
         q = pairs.numel() // 2
         if out is None:
             out = torch.empty(q, dtype=torch.int32, device=pairs.device)
         _dev(out, torch.int32, "out")
+        if out.numel() < q or out.device != pairs.device:
+            raise ValueError(f"out must hold at least {q} int32 on {pairs.device}")
         _check(_lib().plb_query_batch(self.handle, pairs.data_ptr(), q, out.data_ptr() if q else None,
                                       _stream(stream)), "plb_query_batch")
         return out
@@ -383,10 +387,14 @@ def query_directed(l_out: Labels, l_in: Labels, pairs: torch.Tensor, out: torch.
                    stream=None) -> torch.Tensor:
     """d(s -> t) for CUDA int32 pairs [q, 2] from the two sets of build_directed."""
     pairs = _dev(pairs.reshape(-1), torch.int32, "pairs")
+    if pairs.numel() % 2:
+        raise ValueError("pairs must hold an even number of ids (s, t)")
     q = pairs.numel() // 2
     if out is None:
         out = torch.empty(q, dtype=torch.int32, device=pairs.device)
     _dev(out, torch.int32, "out")
+    if out.numel() < q or out.device != pairs.device:
+        raise ValueError(f"out must hold at least {q} int32 on {pairs.device}")
     _check(_lib().plb_query_directed(l_out.handle, l_in.handle, pairs.data_ptr(), q, out.data_ptr() if q else None,
                                      _stream(stream)), "plb_query_directed")
     return out
@@ -401,9 +409,18 @@ def query_multi(sets: Sequence[Labels], set_idx: torch.Tensor, pairs: torch.Tens
         arr[i] = s.handle
     pairs = _dev(pairs.reshape(-1), torch.int32, "pairs")
     _dev(set_idx, torch.int32, "set_idx")
+    if pairs.numel() % 2:
+        raise ValueError("pairs must hold an even number of ids (s, t)")
     q = pairs.numel() // 2
+    if set_idx.numel() != q:
+        raise ValueError(f"set_idx must have one entry per pair ({q}), got {set_idx.numel()}")
+    if set_idx.device != pairs.device:
+        raise ValueError("set_idx and pairs must be on the same device")
     if out is None:
         out = torch.empty(q, dtype=torch.int32, device=pairs.device)
+    _dev(out, torch.int32, "out")
+    if out.numel() < q or out.device != pairs.device:
+        raise ValueError(f"out must hold at least {q} int32 on {pairs.device}")
     _check(_lib().plb_query_multi(arr, m, set_idx.data_ptr() if q else None, pairs.data_ptr() if q else None, q,
                                   out.data_ptr() if q else None, _stream(stream)), "plb_query_multi")
     return out
@@ -433,6 +450,8 @@ def degree_order_noalloc(row_ptr: torch.Tensor, out: torch.Tensor | None = None,
     if out is None:
         out = torch.empty(n, dtype=torch.int32, device=row_ptr.device)
     _dev(out, torch.int32, "out")
+    if out.numel() < n or out.device != row_ptr.device:
+        raise ValueError(f"out must hold at least {n} int32 on {row_ptr.device}")
     g = CSR(n, 0, row_ptr.data_ptr(), None)
     _check(_lib().plb_degree_order_noalloc(ctypes.byref(g), out.data_ptr() if n else None, _stream(stream)),
            "plb_degree_order_noalloc")

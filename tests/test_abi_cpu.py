@@ -96,3 +96,48 @@ def test_binding_refuses_host_tensors():
         plb.build_weighted(off, col, torch.zeros(0, dtype=torch.uint8), torch.zeros(1, dtype=torch.int32))
     with pytest.raises(TypeError):
         plb.build_directed(off, col, torch.zeros(1, dtype=torch.int32))
+
+
+def test_binding_checks_buffer_sizes_before_calling_the_library(monkeypatch):
+    """Short output buffers, a set index per pair and an odd id count are
+    refused on the host: the library would otherwise write past a buffer."""
+    torch = pytest.importorskip("torch")
+    from paper_1906_12018_gb300 import plb
+
+    calls = []
+
+    class FakeLib:
+        def __getattr__(self, name):
+            def f(*a):
+                calls.append(name)
+                return 0
+            return f
+
+    monkeypatch.setattr(plb, "_dev", lambda t, dtype, name: t)   # host tensors stand in for device ones
+    monkeypatch.setattr(plb, "_lib", lambda: FakeLib())
+    monkeypatch.setattr(plb, "_stream", lambda s: 0)
+    i32 = torch.int32
+    rp = torch.zeros(11, dtype=torch.int64)                         # n = 10
+    with pytest.raises(ValueError):
+        plb.degree_order_noalloc(rp, out=torch.empty(9, dtype=i32))
+    with pytest.raises(ValueError):
+        plb.degree_order_noalloc(rp, out=torch.empty(10, dtype=i32, device="meta"))
+    lab = object.__new__(plb.Labels)
+    lab._h = ctypes.c_void_p(1)
+    with pytest.raises(ValueError):
+        lab.query(torch.zeros(7, dtype=i32))
+    with pytest.raises(ValueError):
+        lab.query(torch.zeros(8, dtype=i32), out=torch.empty(3, dtype=i32))
+    with pytest.raises(ValueError):
+        plb.query_directed(lab, lab, torch.zeros(8, dtype=i32), out=torch.empty(3, dtype=i32))
+    with pytest.raises(ValueError):
+        plb.query_multi([lab], torch.zeros(4, dtype=i32), torch.zeros(7, dtype=i32))
+    with pytest.raises(ValueError):
+        plb.query_multi([lab], torch.zeros(3, dtype=i32), torch.zeros(8, dtype=i32))
+    with pytest.raises(ValueError):
+        plb.query_multi([lab], torch.zeros(4, dtype=i32), torch.zeros(8, dtype=i32), out=torch.empty(3, dtype=i32))
+    assert calls == []
+    # well-formed calls reach the library
+    plb.degree_order_noalloc(rp, out=torch.empty(10, dtype=i32))
+    plb.query_multi([lab], torch.zeros(4, dtype=i32), torch.zeros(8, dtype=i32), out=torch.empty(4, dtype=i32))
+    assert calls == ["plb_degree_order_noalloc", "plb_query_multi"]

@@ -206,6 +206,26 @@ def test_query_equals_apsp(name, g):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("name,g", tiny_graphs(), ids=lambda x: x if isinstance(x, str) else "")
+def test_bfs_equals_apsp(name, g):
+    """The textbook BFS that checks sampled GPU queries on the large
+    workloads, pinned to scipy's all-pairs distances from every source."""
+    D = apsp(g)
+    for s in range(g.n):
+        want = np.where(np.isfinite(D[s]), D[s], -1).astype(np.int64)
+        assert np.array_equal(O.bfs(g.off, g.col, s), want), (name, s)
+
+
+def test_bfs_equals_scipy_on_rmat12():
+    g = G.workload("rmat12")
+    a = sp.csr_matrix((np.ones(g.nnz), g.col, g.off), shape=(g.n, g.n))
+    src = [0, 1, 17, g.n // 2, g.n - 1]
+    D = shortest_path(a, method="D", unweighted=True, directed=False, indices=src)
+    for i, s in enumerate(src):
+        want = np.where(np.isfinite(D[i]), D[i], -1).astype(np.int64)
+        assert np.array_equal(O.bfs(g.off, g.col, s), want), s
+
+
 # ----------------------------------------------------- R-MAT 2^12 workload
 @pytest.fixture(scope="module")
 def rmat12():
