@@ -142,6 +142,11 @@ typedef struct {
        escalated vertices), [2] 0 */
     double ms_total, ms_prepare, ms_frontier, ms_gather_prune[3], ms_merge, ms_finalize;
     int64_t launches;               /* kernels launched by this build */
+    /* profile = 1 only (else 0): over the candidates (h, d) checked at v, the label entries the
+       distance check reads by the cost model of Sec. 4.3: the entries of L(v) with hub < h (the
+       side the paper scans), and |L(h)| (the side it hashes) */
+    int64_t check_lv_entries;
+    int64_t check_lh_entries;
 } plb_build_stats;
 
 /* Fill *opt with defaults. */

@@ -257,6 +257,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.gscratch_words = std::max<int64_t>(n, 1);
         p.rbound = rbound;
         p.stage_ratio = o.warp_stage_ratio;
+        p.count_check = o.profile != 0;
         p.unsorted = U;
         return p;
     };
@@ -464,6 +465,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         st.unique_candidates += (int64_t)hctr->uniq;
         st.staged_entries += (int64_t)hctr->staged;
         st.probed_entries += (int64_t)hctr->probed;
+        st.check_lv_entries += (int64_t)hctr->chk_lv;
+        st.check_lh_entries += (int64_t)hctr->chk_lh;
         for (int k = 0; k < 3; ++k) st.tier_vertices[k] += (int64_t)hctr->tier[k];
         if (acc == 0) {
             finished = true;
@@ -717,6 +720,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                 st.unique_candidates += x.uniq;
                 st.staged_entries += x.staged;
                 st.probed_entries += x.probed;
+                st.check_lv_entries += x.chk_lv;
+                st.check_lh_entries += x.chk_lh;
                 st.tier_vertices[0] += x.tier0;
                 st.tier_vertices[1] += x.tier1;
             }

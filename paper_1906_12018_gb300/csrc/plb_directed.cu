@@ -308,6 +308,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
         p.log_m = w_log_m;
         p.cand_limit = warp_cand;
         p.stage_ratio = o.warp_stage_ratio;
+        p.count_check = o.profile != 0;
         p.unsorted = S.U;
         k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
         p.list = S.O1;
@@ -441,6 +442,8 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
             S.st.unique_candidates += (int64_t)h.uniq;
             S.st.staged_entries += (int64_t)h.staged;
             S.st.probed_entries += (int64_t)h.probed;
+            S.st.check_lv_entries += (int64_t)h.chk_lv;
+            S.st.check_lh_entries += (int64_t)h.chk_lh;
             for (int q = 0; q < 3; ++q) S.st.tier_vertices[q] += (int64_t)h.tier[q];
             S.rounds = d;
             if (acc == 0) S.done = true;

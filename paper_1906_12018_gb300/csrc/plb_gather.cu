@@ -76,17 +76,25 @@ __device__ __forceinline__ void stage_exact_levels(const uint32_t* top, int32_t 
 __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, const uint32_t* M, int log_m,
                                                 bool mv_global, int b_min, int b_shift, const uint32_t* lv,
                                                 int64_t lvlen, uint32_t h, bool valid, unsigned long long& probed,
-                                                const uint32_t* tv, unsigned long long& prefiltered) {
+                                                const uint32_t* tv, unsigned long long& prefiltered,
+                                                unsigned long long* chk) {
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
     if (valid) {
+        // the row bounds and the probe-table descriptor of h are loaded
+        // together (independent loads, one round trip)
         const int64_t hb = p.loff_h[h];
-        const int la = (int)(p.loff_h[h + 1] - hb) - 1;
+        const int64_t he = p.loff_h[h + 1];
+        const uint64_t hd = p.hdesc_h[h];
+        const int la = (int)(he - hb) - 1;
         base = hb;
         items = la;
+        if (p.count_check) {  // the cost model's reads: L(v)'s entries below h, and L(h)
+            chk[0] += (unsigned long long)lower_bound_u32(lv, lvlen, pack(h, 0));
+            chk[1] += (unsigned long long)(la + 1);
+        }
         if (la >= b_min) {
-            const uint64_t hd = p.hdesc_h[h];
             if (hd) {
                 const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
                 if (mv_global ? lb < la : (lb << b_shift) < la) {
@@ -109,28 +117,37 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
     const int total = __shfl_sync(kFull, incl, 31);
     const int excl = incl - items;
     unsigned pm = 0;  // candidates with a witness so far (the same in every lane)
-    for (int ib = 0; ib < total; ib += 32) {
+    // kCheckUnroll items per lane per step: their entry loads (side A: L(h);
+    // side B: L(v)) are all issued before any lookup uses one
+    for (int ib = 0; ib < total; ib += 32 * kCheckUnroll) {
         if ((pm & vmask) == vmask) break;
-        const int it = ib + lane;
-        const int k = warp_owner(excl, it);
-        const int64_t bk = __shfl_sync(kFull, base, k);
-        const int exk = __shfl_sync(kFull, excl, k);
-        const int mk = __shfl_sync(kFull, meta, k);
-        bool hit = false;
-        if (it < total && !((pm >> k) & 1u)) {
-            const int j = it - exk;
-            if (mk == 0) {
-                const uint32_t x = p.lent_h[bk + j];
-                const uint32_t dv = map_find(M, log_m, hub_of(x));
-                hit = dv != kEmpty && dv + dist_of(x) <= d;
-            } else {
-                const uint32_t y = lv[j];
-                const uint32_t dh = map_find(p.htab_h + bk, mk - 1, hub_of(y));
-                hit = dh != kEmpty && dh + dist_of(y) <= d;
-            }
+        int ku[kCheckUnroll], mku[kCheckUnroll];
+        int64_t bku[kCheckUnroll];
+        uint32_t xu[kCheckUnroll];
+#pragma unroll
+        for (int u = 0; u < kCheckUnroll; ++u) {
+            const int it = ib + 32 * u + lane;
+            const int k = warp_owner(excl, it);
+            bku[u] = __shfl_sync(kFull, base, k);
+            const int exk = __shfl_sync(kFull, excl, k);
+            mku[u] = __shfl_sync(kFull, meta, k);
+            ku[u] = (it < total && !((pm >> k) & 1u)) ? k : -1;
+            xu[u] = kEmpty;
+            if (ku[u] >= 0) xu[u] = mku[u] == 0 ? p.lent_h[bku[u] + (it - exk)] : lv[it - exk];
+        }
+        unsigned hits = 0;
+#pragma unroll
+        for (int u = 0; u < kCheckUnroll; ++u) {
+            if (ku[u] < 0) continue;
+            const uint32_t x = xu[u];
+            // side A: x is an entry of L(h), looked up in L(v)'s map; side B:
+            // x is an entry of L(v), looked up in h's probe table
+            const uint32_t dw = mku[u] == 0 ? map_find(M, log_m, hub_of(x))
+                                            : map_find(p.htab_h + bku[u], mku[u] - 1, hub_of(x));
+            if (dw != kEmpty && dw + dist_of(x) <= d) hits |= 1u << ku[u];
             ++probed;
         }
-        pm |= __reduce_or_sync(kFull, hit ? 1u << k : 0u);
+        pm |= __reduce_or_sync(kFull, hits);
     }
     return vmask & ~pm;
 }
@@ -273,14 +290,18 @@ __device__ void shrink_pass(uint32_t* S, int log_s, uint32_t* C, int limit, uint
 // neighbour's sub-range of dL_{d-1}(a) (binary searches in the sorted row), a
 // block-wide exclusive scan of the counts assigns every thread an equal,
 // contiguous share of the tile's messages.  When the set would exceed
-// `limit`, its range (hubs >= W) is shrunk (shrink_pass) and the current tile
-// redone, so messages gathered below the new bound are kept.
+// `limit`, its range (hubs >= W) is shrunk (shrink_pass: S keeps the keys
+// below the new bound) and every warp resumes its share of the tile from the
+// step where it stopped, now dropping hubs at or above the new bound (a later
+// pass takes them): no message of the tile is read twice, except those of
+// the step that met the overflow.
 __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t lo, uint32_t* hi_sm, uint8_t* B,
                              uint32_t W, uint32_t* S, int log_s, const uint32_t* M, int log_m, int limit, int* cnt_sm,
                              volatile int* ovf_sm, int* wsum, int* sex, int64_t* sst, uint32_t* C, int* hist, int* tmp,
                              unsigned long long& msgs) {
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int64_t t0 = nb; t0 < ne;) {
+    const int nw = nthr >> 5, lane = tid & 31;
+    for (int64_t t0 = nb; t0 < ne; t0 += nthr) {
         const uint32_t hi = *(volatile uint32_t*)hi_sm;
         const int64_t j = t0 + tid;
         int c = 0;
@@ -316,63 +337,71 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
         // it in windows of 32 rows: lane j holds the start of row k0 + j, and
         // 32 consecutive messages at a time find their row by a warp-shuffle
         // search, so that the lanes of a load read consecutive hubs of a row
-        const int nw = nthr >> 5, lane = tid & 31;
         const int per_w = (((total + nw - 1) / nw) + 31) & ~31;
         const int wbeg = (tid >> 5) * per_w, wend = min(total, wbeg + per_w);
-        if (wbeg < wend) {
-            int k0 = 0, hk = nne - 1;  // row of wbeg: largest k with sex[k] <= wbeg
-            while (k0 < hk) {
-                const int mid = (k0 + hk + 1) >> 1;
-                if (sex[mid] <= wbeg) k0 = mid; else hk = mid - 1;
-            }
-            bool stop = false;
-            for (int it0 = wbeg; it0 < wend && !stop; k0 += 32) {
-                const int kr = k0 + lane;
-                const int ex = kr < nne ? sex[kr] : total;
-                const int64_t stv = kr < nne ? sst[kr] : 0;
-                const int wcap = k0 + 32 < nne ? sex[k0 + 32] : total;
-                const int wend_w = min(wend, wcap);
-                for (int ib = it0; ib < wend_w; ib += 32 * kGatherUnroll) {
-                    uint32_t hv[kGatherUnroll];
+        int pos = wbeg;  // this warp's messages before pos are done
+        while (true) {
+            // hubs at or above hcut are left to a later pass (hcut = hi
+            // until the set's range shrinks within this tile)
+            const uint32_t hcut = *(volatile uint32_t*)hi_sm;
+            if (pos < wend) {
+                int k0 = 0, hk = nne - 1;  // row of pos: largest k with sex[k] <= pos
+                while (k0 < hk) {
+                    const int mid = (k0 + hk + 1) >> 1;
+                    if (sex[mid] <= pos) k0 = mid; else hk = mid - 1;
+                }
+                bool stop = false;
+                for (int it0 = pos; it0 < wend && !stop; k0 += 32) {
+                    const int kr = k0 + lane;
+                    const int ex = kr < nne ? sex[kr] : total;
+                    const int64_t stv = kr < nne ? sst[kr] : 0;
+                    const int wcap = k0 + 32 < nne ? sex[k0 + 32] : total;
+                    const int wend_w = min(wend, wcap);
+                    for (int ib = it0; ib < wend_w; ib += 32 * kGatherUnroll) {
+                        uint32_t hv[kGatherUnroll];
 #pragma unroll
-                    for (int u = 0; u < kGatherUnroll; ++u) {
-                        const int it = ib + 32 * u + lane;
-                        const int kk = warp_owner(ex, it);
-                        const int exk = __shfl_sync(kFull, ex, kk);
-                        const int64_t stk = __shfl_sync(kFull, stv, kk);
-                        hv[u] = it < wend_w ? p.fhub[stk + (it - exk)] : kEmpty;
-                    }
-                    int nins = 0;
+                        for (int u = 0; u < kGatherUnroll; ++u) {
+                            const int it = ib + 32 * u + lane;
+                            const int kk = warp_owner(ex, it);
+                            const int exk = __shfl_sync(kFull, ex, kk);
+                            const int64_t stk = __shfl_sync(kFull, stv, kk);
+                            hv[u] = it < wend_w ? p.fhub[stk + (it - exk)] : kEmpty;
+                        }
+                        int nins = 0;
 #pragma unroll
-                    for (int u = 0; u < kGatherUnroll; ++u) {
-                        const uint32_t h = hv[u];
-                        if (h < W) {
-                            B[h] = 1;
-                        } else if (h != kEmpty && (!M || map_find(M, log_m, h) == kEmpty)) {
-                            if (*(volatile int*)cnt_sm >= limit) *ovf_sm = 1;
-                            else nins += set_insert(S, log_s, h) ? 1 : 0;
+                        for (int u = 0; u < kGatherUnroll; ++u) {
+                            const uint32_t h = hv[u];
+                            if (h < W) {
+                                B[h] = 1;
+                            } else if (h < hcut && (!M || map_find(M, log_m, h) == kEmpty)) {
+                                if (*(volatile int*)cnt_sm >= limit) *ovf_sm = 1;
+                                else nins += set_insert(S, log_s, h) ? 1 : 0;
+                            }
+                        }
+                        nins = warp_sum(nins);
+                        if (lane == 0 && nins) atomicAdd(cnt_sm, nins);
+                        if (__any_sync(kFull, *ovf_sm != 0)) {
+                            stop = true;  // resume from this step after the shrink
+                            pos = ib;
+                            break;
                         }
                     }
-                    nins = warp_sum(nins);
-                    if (lane == 0 && nins) atomicAdd(cnt_sm, nins);
-                    if (__any_sync(kFull, *ovf_sm != 0)) {
-                        stop = true;
-                        break;
-                    }
+                    if (!stop) it0 = wend_w;
                 }
-                it0 = wend_w;
+                if (!stop) pos = wend;
             }
+            __syncthreads();
+            // concurrent inserts can pass the limit without raising the flag
+            if (*ovf_sm || *(volatile int*)cnt_sm > limit) {
+                shrink_pass(S, log_s, C, limit, lo > W ? lo : W, hi_sm, cnt_sm, hist, tmp);  // S holds hubs >= W
+                if (tid == 0) *ovf_sm = 0;
+                __syncthreads();
+                continue;  // every warp resumes at its pos with the smaller range
+            }
+            break;
         }
         if (tid == 0) msgs += total;
-        __syncthreads();
-        // concurrent inserts can pass the limit without raising the flag
-        if (*ovf_sm || *(volatile int*)cnt_sm > limit) {
-            shrink_pass(S, log_s, C, limit, lo > W ? lo : W, hi_sm, cnt_sm, hist, tmp);  // S holds hubs >= W
-            if (tid == 0) *ovf_sm = 0;
-            __syncthreads();
-            continue;  // redo this tile with the smaller range
-        }
-        t0 += nthr;
+        __syncthreads();  // sex / sst are rewritten by the next tile
     }
 }
 
@@ -394,7 +423,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
     uint32_t* S = tvs + nwarps * kTopRow + wib * (S_CAP + M_CAP);
     uint32_t* M = S + S_CAP;
     unsigned long long c_arcs = 0, c_msgs = 0, c_uniq = 0, c_staged = 0, c_probed = 0, c_acc = 0, c_vert = 0;
-    unsigned long long c_pref = 0;
+    unsigned long long c_pref = 0, c_chk[2] = {0, 0};
     if (p.ctr->done) return;
     const uint32_t d = p.ctr->d;
     const int nlist = *p.list_n;
@@ -473,7 +502,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
             const unsigned okm = check_chunk(p, d, Mv, log_m, mglob, kWarpSideBMin, kWarpSideBShift, lvp, ll, h,
-                                             valid, c_probed, tv, c_pref);
+                                             valid, c_probed, tv, c_pref, c_chk);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
@@ -519,6 +548,14 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
     }
     c_probed = warp_sum(c_probed);
     c_msgs = warp_sum(c_msgs);
+    if (p.count_check) {
+        c_chk[0] = warp_sum(c_chk[0]);
+        c_chk[1] = warp_sum(c_chk[1]);
+        if (lane == 0) {
+            atomicAdd(&p.ctr->chk_lv, c_chk[0]);
+            atomicAdd(&p.ctr->chk_lh, c_chk[1]);
+        }
+    }
     if (lane == 0) {
         atomicAdd(&p.ctr->arcs, c_arcs);
         atomicAdd(&p.ctr->msgs, c_msgs);
@@ -619,6 +656,16 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
                 else p.ctr->guard = 1;  // invariant broken: report instead of writing out of bounds
             }
         }
+        __syncthreads();  // every warp has read the set
+        // L(v)'s sorted row in the set's free tail (the byte-map staging below
+        // uses its head): the checks' binary searches in L(v) and their side-B
+        // scans of it then read shared memory
+        const uint32_t* lvp = lv;
+        if (ll + (int64_t)nw * kByteStage <= (int64_t)S_CAP) {
+            uint32_t* lvs = S + (S_CAP - ll);
+            for (int64_t j = tid; j < ll; j += nthr) lvs[j] = lv[j];
+            lvp = lvs;
+        }
         __syncthreads();
         const int nc_set = min(*(volatile int*)&sh[SH_NC], limit);  // candidates from the set
         if (tid == 0) cnt[2] += nc_set;
@@ -644,8 +691,8 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
                 const int nchk = f & ~31;
                 for (int cb = 0; cb < nchk; cb += 32) {
                     const uint32_t h = stage[cb + lane];
-                    const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lv,
-                                                     ll, h, true, cnt[4], tv, cnt[7]);
+                    const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lvp,
+                                                     ll, h, true, cnt[4], tv, cnt[7], cnt + 8);
                     int base = 0;
                     if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
                     base = __shfl_sync(kFull, base, 0);
@@ -672,10 +719,16 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
         for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
             bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
-            // without the map, set candidates may be hubs of v already
-            if (!useM && valid && cb + lane < nc_set && map_find(Mp, log_mp, h) != kEmpty) valid = false;
-            const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lv, ll, h,
-                                             valid, cnt[4], tv, cnt[7]);
+            // without the map, set candidates may be hubs of v already (they
+            // were counted as unique candidates: take them back)
+            if (!useM) {
+                const bool known = valid && cb + lane < nc_set && map_find(Mp, log_mp, h) != kEmpty;
+                const unsigned km = __ballot_sync(kFull, known);
+                if (lane == 0) cnt[2] -= __popc(km);
+                if (known) valid = false;
+            }
+            const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lvp, ll, h,
+                                             valid, cnt[4], tv, cnt[7], cnt + 8);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
             base = __shfl_sync(kFull, base, 0);
@@ -722,7 +775,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_block(GpParams p) {
     uint32_t* C = M + (1 << p.log_m);
     uint8_t* B = reinterpret_cast<uint8_t*>(C + p.cand_limit + (int)blockDim.x);  // kByteHubs bytes
     uint32_t* gacc = p.gscratch + (int64_t)blockIdx.x * p.gscratch_words;
-    unsigned long long cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long cnt[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (p.ctr->done) return;
     const uint32_t d = p.ctr->d;
     const int n1 = *p.list_n;
@@ -732,6 +785,14 @@ __global__ void __launch_bounds__(256, 3) k_gp_block(GpParams p) {
     }
     cnt[1] = warp_sum(cnt[1]);
     cnt[4] = warp_sum(cnt[4]);
+    if (p.count_check) {
+        cnt[8] = warp_sum(cnt[8]);
+        cnt[9] = warp_sum(cnt[9]);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&p.ctr->chk_lv, cnt[8]);
+            atomicAdd(&p.ctr->chk_lh, cnt[9]);
+        }
+    }
     if ((threadIdx.x & 31) == 0) {  // lane 0 of each warp holds its warp's unique and prefiltered counts
         atomicAdd(&p.ctr->msgs, cnt[1]);
         atomicAdd(&p.ctr->probed, cnt[4]);

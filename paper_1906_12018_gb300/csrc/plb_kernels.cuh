@@ -30,6 +30,8 @@ struct RoundCounters {
     unsigned long long tier[3];
     unsigned long long bound_sum; // sum over receivers of the candidate bound min(v, messages)
     unsigned long long prefiltered; // candidates pruned by the top-hub witness prefilter
+    unsigned long long chk_lv, chk_lh;  // checked candidates (h at v): sums of |L(v) entries with hub < h|
+                                        // and of |L(h)| (counted when GpParams::count_check is set)
     int nR, nO1, nO2;             // receivers: warp tier, block tier (nO2 unused)
     int nBig, nGiant;             // new frontier rows too long for a warp / for shared memory to sort
     int nU;                       // vertices whose new frontier row was written unsorted (block tier)
@@ -60,7 +62,7 @@ constexpr int kStopIndex = 3;
 
 // Per-round statistics written on the device (graph mode).
 struct RoundStat {
-    long long receivers, accepted, uniq, probed, msgs, pref, arcs, staged, tier0, tier1;
+    long long receivers, accepted, uniq, probed, msgs, pref, arcs, staged, tier0, tier1, chk_lv, chk_lh;
 };
 
 struct GpParams {
@@ -102,6 +104,8 @@ struct GpParams {
                                // count ctr->nU), or null (every new row is sorted after the round)
     int sender_bits;           // rcol holds frontier descriptor indices whose low sender_bits bits are
                                // the sending vertex (weighted rounds), or 0: the vertex itself
+    int count_check;           // 1: count the label entries each check would read by the paper's cost
+                               // model (RoundCounters::chk_lv / chk_lh; one binary search per candidate)
 };
 
 // The sending vertex of an arc's descriptor index (see GpParams::sender_bits).
@@ -127,6 +131,8 @@ constexpr int kTopRow = kTopLevels * kTopWords;      // words per vertex
 // Messages each lane loads before inserting them (gathers keep several loads
 // in flight per warp).
 constexpr int kGatherUnroll = 4;
+// Label entries each lane loads per step of a distance check.
+constexpr int kCheckUnroll = 2;
 
 // Block tier: hubs below this rank are deduplicated in a shared-memory byte
 // map (one byte per hub) instead of the hash set.

@@ -379,7 +379,7 @@ __global__ void k_rerun_reset(RoundCounters* ctr, uint64_t* fse_new, int64_t n) 
         ctr->accepted = 0;
         ctr->fovf = 0;
         ctr->nU = 0;
-        ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = 0;
+        ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = ctr->chk_lv = ctr->chk_lh = 0;
         ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;
     }
 }
@@ -751,6 +751,8 @@ __global__ void k_g_check(RoundCounters* ctr, RoundStat* stats) {
         r.msgs = (long long)ctr->msgs;
         r.pref = (long long)ctr->prefiltered;
         r.arcs = (long long)ctr->arcs;
+        r.chk_lv = (long long)ctr->chk_lv;
+        r.chk_lh = (long long)ctr->chk_lh;
         r.staged = (long long)ctr->staged;
         r.tier0 = (long long)ctr->tier[0];
         r.tier1 = (long long)ctr->tier[1];
@@ -781,7 +783,7 @@ __global__ void k_g_finish(RoundCounters* ctr) {
         ctr->done = 1;
     }
     ctr->cur ^= 1;
-    ctr->cursor = ctr->accepted = ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = 0;
+    ctr->cursor = ctr->accepted = ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = ctr->chk_lv = ctr->chk_lh = 0;
     ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;
     ctr->bound_sum = ctr->prefiltered = 0;
     ctr->nR = ctr->nO1 = ctr->nO2 = ctr->nBig = ctr->nGiant = ctr->nU = 0;

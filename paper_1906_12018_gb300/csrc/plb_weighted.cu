@@ -166,7 +166,7 @@ __global__ void k_w_rerun(RoundCounters* ctr, uint64_t* fse_new, int64_t n, unsi
         ctr->accepted = 0;
         ctr->fovf = 0;
         ctr->nU = 0;
-        ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = ctr->prefiltered = 0;
+        ctr->arcs = ctr->msgs = ctr->uniq = ctr->staged = ctr->probed = ctr->prefiltered = ctr->chk_lv = ctr->chk_lh = 0;
         ctr->tier[0] = ctr->tier[1] = ctr->tier[2] = 0;
     }
 }
@@ -431,6 +431,7 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
         p.log_m = w_log_m;
         p.cand_limit = warp_cand;
         p.stage_ratio = o.warp_stage_ratio;
+        p.count_check = o.profile != 0;
         p.unsorted = U;
         k_gp_warp<<<grid_w, kGpWarpThreads, w_smem, s>>>(p);
         p.list = O1;
@@ -506,6 +507,8 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
             st.unique_candidates += (int64_t)hctr->uniq;
             st.staged_entries += (int64_t)hctr->staged;
             st.probed_entries += (int64_t)hctr->probed;
+            st.check_lv_entries += (int64_t)hctr->chk_lv;
+            st.check_lh_entries += (int64_t)hctr->chk_lh;
             for (int q = 0; q < 3; ++q) st.tier_vertices[q] += (int64_t)hctr->tier[q];
         }
         rounds = d;

@@ -104,6 +104,8 @@ class BuildStats(ctypes.Structure):
         ("ms_merge", ctypes.c_double),
         ("ms_finalize", ctypes.c_double),
         ("launches", ctypes.c_int64),
+        ("check_lv_entries", ctypes.c_int64),
+        ("check_lh_entries", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:
@@ -134,6 +136,8 @@ class BuildStats(ctypes.Structure):
             "ms_merge": self.ms_merge,
             "ms_finalize": self.ms_finalize,
             "launches": self.launches,
+            "check_lv_entries": self.check_lv_entries,
+            "check_lh_entries": self.check_lh_entries,
         }
 
 
