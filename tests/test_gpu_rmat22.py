@@ -1,7 +1,13 @@
 """R-MAT scale 22 (edge factor 16, seed 3, LCC: 2.39M vertices, 64.2M edges,
-1.8G labels), the serving workload, at full size with the default launch
-configuration: sampled rows against Def. 2, sampled queries against BFS, and
-the row invariants over every label (checked on the device, in slices)."""
+1.8G labels), the largest workload and the serving one, at full size with
+the default launch configuration: every row against the stored digests of
+the oracle's full PLL run, about 2,000 rows stratified by rank and degree
+against Def. 2, sampled queries against BFS, and the row invariants over
+every label (checked on the device, in slices)."""
+import json
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -10,6 +16,10 @@ torch = pytest.importorskip("torch")
 import oracle as O  # noqa: E402
 from gpu_util import gpu_build, gpu_query  # noqa: E402
 from paper_1906_12018_gb300 import graphs as G  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+sys.path.insert(0, GOLDEN)
+import label_digest as LD  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -30,18 +40,59 @@ def test_rmat22_size(rmat22):
     assert lab.total == 1799946086
 
 
-def test_rmat22_sampled_rows_match_definition(rmat22):
+def stratified_rows(g, order, per=32, seed=22):
+    """Rows to compare with Def. 2: the 512 highest-ranked vertices, `per`
+    random vertices from each of 16 equal rank strata and from each of 16
+    degree-quantile strata, and 512 uniform picks (2,048 distinct rows at
+    most)."""
+    rng = np.random.default_rng(seed)
+    n = g.n
+    picks = set(int(x) for x in order[:512])
+    for s in range(16):
+        lo, hi = s * n // 16, (s + 1) * n // 16
+        picks.update(int(x) for x in order[rng.integers(lo, hi, per)])
+    by_deg = np.argsort(g.degrees(), kind="stable")
+    for s in range(16):
+        lo, hi = s * n // 16, (s + 1) * n // 16
+        picks.update(int(x) for x in by_deg[rng.integers(lo, hi, per)])
+    picks.update(int(x) for x in rng.choice(n, 512, replace=False))
+    return sorted(picks)
+
+
+def test_rmat22_stratified_rows_match_definition(rmat22):
+    """About 2,000 rows stratified by rank and degree equal Def. 2, each
+    computed by its own BFS (the oracle's Def. 2 row function, run on host
+    threads)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     g, order, lab = rmat22
     off_d, hub_d, dist_d = lab.device_arrays()
     off = off_d.cpu().numpy()
-    rng = np.random.default_rng(22)
-    deg = g.degrees()
-    picks = list(rng.choice(g.n, 10, replace=False)) + list(order[:3]) + list(np.argsort(-deg)[500:503])
-    for v in picks:
-        h, d = O.chhl_row(g.off, g.col, order, int(v))
+    rows = stratified_rows(g, order)
+    assert len(rows) >= 1500
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        want = list(ex.map(lambda v: O.chhl_row(g.off, g.col, order, v), rows))
+    for v, (h, d) in zip(rows, want):
         a, b = int(off[v]), int(off[v + 1])
         assert np.array_equal(hub_d[a:b].cpu().numpy().astype(np.uint32), h), v
         assert np.array_equal(dist_d[a:b].cpu().numpy(), d), v
+
+
+def test_rmat22_all_labels_equal_oracle_digests(rmat22):
+    """Every row: the GPU labels digested per block of 2^16 rows equal the
+    stored digests of the oracle's full PLL run on this graph
+    (tests/golden/rmat22_labels.json, written by tests/golden/make_digests.py)."""
+    path = os.path.join(GOLDEN, "rmat22_labels.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle digests of rmat22 not recorded")
+    with open(path) as f:
+        want = json.load(f)
+    g, order, lab = rmat22
+    assert (g.n, g.m, lab.total) == (want["n"], want["m"], want["labels"])
+    off, hub, dist = lab.to_host()
+    got = LD.block_digests(off, hub, dist, want["block_rows"])
+    bad = [i for i, (a, b) in enumerate(zip(got, want["blocks"])) if a != b]
+    assert len(got) == len(want["blocks"]) and bad == []
 
 
 def test_rmat22_sampled_queries_match_bfs(rmat22):
