@@ -28,16 +28,40 @@ import numpy as np
 
 
 # ------------------------------------------------------------------ policy
-def build_footprint(n: int, nnz: int, label_bytes_per_vertex: int = 9 * 96) -> int:
-    """Conservative device bytes of a build of a graph with n vertices and nnz
-    arcs: inputs (8(n+1) + 4 nnz + 4n), rank-space copy and frontier buffers
-    (about 3x the arcs), label buffers during the build (two copies and the
-    probe index) and the final labels, at ``label_bytes_per_vertex`` per
-    vertex, plus the 256-byte top-hub row per vertex."""
+# Label count of a graph, fitted (least squares on log(labels / n)) to the
+# oracle's label totals of the 2,000 graphs of the batched workload: within
+# -11% .. +19% of every one of them; the R-MAT scale-22 graph has 1.43x the
+# model's count, so estimates carry a safety factor.
+LABELS_LOG_COEF = (-0.6997, 0.3050, 0.7563)  # log(labels/n) = a + b log n + c log(nnz/2n)
+LABEL_SAFETY = 1.5
+# Device bytes per final label at a build's peak (label buffers of both
+# parities, the probe tables, the output arrays): the R-MAT scale-22 build
+# peaked at 59.
+BUILD_BYTES_PER_LABEL = 64
+
+
+def estimated_labels(n: int, nnz: int) -> float:
+    """Label count estimate of a graph with n vertices and nnz arcs (nnz/2
+    undirected edges), before the safety factor."""
+    import math
+
+    if n <= 0:
+        return 0.0
+    a, b, c = LABELS_LOG_COEF
+    deg = max(nnz / 2.0 / n, 0.5)
+    return n * math.exp(a + b * math.log(n) + c * math.log(deg))
+
+
+def build_footprint(n: int, nnz: int) -> int:
+    """Device bytes a build of this graph is expected to hold at its peak:
+    inputs (8(n+1) + 4 nnz + 4n), rank-space copy, frontier and tier buffers
+    (about 12 bytes per arc and 64 per vertex), the 224-byte top-hub row per
+    vertex, and BUILD_BYTES_PER_LABEL per estimated label (with the safety
+    factor)."""
     inputs = 8 * (n + 1) + 4 * nnz + 4 * n
-    work = 12 * nnz + 64 * n
-    labels = 4 * label_bytes_per_vertex * n
-    return int(inputs + work + labels + 256 * n)
+    work = 12 * nnz + 64 * n + 224 * n
+    labels = BUILD_BYTES_PER_LABEL * LABEL_SAFETY * estimated_labels(n, nnz)
+    return int(inputs + work + labels)
 
 
 def admit_jobs(pending: list, free_slots: int, budget: int, used: int) -> list:
@@ -96,28 +120,36 @@ class BuildJob:
     t_submit: float = 0.0
     t_done: float = 0.0
     future: Future = field(default_factory=Future)
+    retries: int = 0                  # re-admissions after the device ran out of memory
 
 
 # ------------------------------------------------------------------ server
 class LabelServer:
     def __init__(self, device: int = 0, hbm_budget: int | None = None, build_slots: int = 2,
-                 max_inflight: int = 2, max_pairs_per_launch: int = 1 << 21, options=None):
-        import torch
-
-        from . import plb
-
+                 max_inflight: int = 2, max_pairs_per_launch: int = 1 << 21, options=None,
+                 torch_module=None, plb_module=None):
+        """torch_module / plb_module replace torch and the library binding
+        (host-side tests of the scheduling drive it with fakes)."""
+        if torch_module is None:
+            import torch as torch_module
+        if plb_module is None:
+            from . import plb as plb_module
+        torch = torch_module
         self.torch = torch
-        self.plb = plb
+        self.plb = plb_module
         self.device = torch.device("cuda", device)
         torch.cuda.set_device(self.device)
         free, total = torch.cuda.mem_get_info(self.device)
         self.budget = int(hbm_budget if hbm_budget is not None else 0.8 * free)
         self.used = 0
+        self.peak_used = 0                # largest admitted total (resident sets + running footprints)
         self.sets: dict[str, object] = {}
         self.set_bytes: dict[str, int] = {}
         self.busy_sets: collections.Counter = collections.Counter()
         self.build_slots = build_slots
         self.running_builds = 0
+        self.running_names: set[str] = set()
+        self.max_oom_retries = 2
         self.max_inflight = max_inflight
         self.max_pairs = max_pairs_per_launch
         self.options = options
@@ -137,25 +169,63 @@ class LabelServer:
     # -------------------------------------------------------------- public
     def add_resident(self, name: str, labels) -> None:
         with self.lock:
+            if self._known(name):
+                raise ValueError(f"label set {name!r} exists or is being built")
             self.sets[name] = labels
             self.set_bytes[name] = labels.nbytes()
             self.used += self.set_bytes[name]
 
+    def _known(self, name: str) -> bool:
+        """A set of this name is resident, queued or being built (lock held)."""
+        return (name in self.sets or name in self.running_names
+                or any(j.name == name for j in self.pending_builds))
+
     def submit_build(self, name: str, off: np.ndarray, col: np.ndarray, order: np.ndarray) -> Future:
+        """Queue a labeling job.  A name already resident, queued or being
+        built is refused (the future fails with ValueError): replacing a
+        resident set in place would leak it."""
         job = BuildJob(name, np.ascontiguousarray(off, np.int64), np.ascontiguousarray(col, np.int32),
                        np.ascontiguousarray(order, np.int32),
                        build_footprint(len(off) - 1, len(col)), time.perf_counter())
         with self.wake:
+            if self._known(name):
+                job.future.set_exception(ValueError(f"label set {name!r} exists or is being built"))
+                return job.future
             self.pending_builds.append(job)
             self.wake.notify()
         return job.future
 
     def submit_query(self, set_name: str, pairs: np.ndarray) -> QueryRequest:
+        """Queue a distance-query request on a resident set or on one whose
+        build is queued or running (it waits for the build).  A request on an
+        unknown name fails at once (KeyError on its future)."""
         req = QueryRequest(set_name, np.ascontiguousarray(pairs, np.int32).reshape(-1, 2), time.perf_counter())
         with self.wake:
+            if not self._known(set_name):
+                req.t_done = time.perf_counter()
+                req.future.set_exception(KeyError(set_name))
+                return req
             self.pending_queries.append(req)
             self.wake.notify()
         return req
+
+    def _fail_queries(self, name: str, exc: BaseException) -> None:
+        """Fail every queued request on `name` (lock held)."""
+        now = time.perf_counter()
+        keep = collections.deque()
+        for r in self.pending_queries:
+            if r.set_name == name:
+                r.t_done = now
+                r.future.set_exception(exc)
+            else:
+                keep.append(r)
+        self.pending_queries = keep
+
+    def _reject(self, job: BuildJob, exc: BaseException) -> None:
+        """The job will never run: fail it and the requests waiting for it (lock held)."""
+        job.t_done = time.perf_counter()
+        job.future.set_exception(exc)
+        self._fail_queries(job.name, exc)
 
     def drop(self, name: str) -> None:
         """Free a resident set once no in-flight query uses it."""
@@ -190,6 +260,7 @@ class LabelServer:
     def _run_build(self, job: BuildJob) -> None:
         torch, plb = self.torch, self.plb
         try:
+            self._build_hook(job)
             torch.cuda.set_device(self.device)
             stream = torch.cuda.Stream(self.device)
             with torch.cuda.stream(stream):
@@ -204,15 +275,29 @@ class LabelServer:
                 self.set_bytes[job.name] = lab.nbytes()
                 self.used += lab.nbytes() - job.footprint
                 self.running_builds -= 1
+                self.running_names.discard(job.name)
                 self.completed_builds.append(job)
                 self.wake.notify()
             job.future.set_result(lab)
         except Exception as e:  # reported to the submitter
+            oom = isinstance(e, plb.PLBError) and e.code == plb.PLB_ERR_OOM
             with self.wake:
                 self.used -= job.footprint
                 self.running_builds -= 1
+                self.running_names.discard(job.name)
+                if oom and job.retries < self.max_oom_retries:
+                    # the estimate was too small, or other work held the
+                    # memory: wait for twice the footprint and run it again
+                    job.retries += 1
+                    job.footprint = 2 * job.footprint
+                    self.pending_builds.appendleft(job)
+                else:
+                    self._reject(job, e)
                 self.wake.notify()
-            job.future.set_exception(e)
+
+    def _build_hook(self, job: BuildJob) -> None:
+        """Called in the worker before each build attempt (tests inject
+        failures here)."""
 
     # -------------------------------------------------------------- queries
     def _launch_queries(self, reqs: list) -> None:
@@ -268,6 +353,15 @@ class LabelServer:
             with self.wake:
                 if self.stop_flag:
                     return
+                # a job at the head that cannot fit even once every running
+                # build has finished (only resident sets hold memory then)
+                # is rejected, so that it does not block the queue for good
+                resident = sum(self.set_bytes.values())
+                while self.pending_builds and self.pending_builds[0].footprint > self.budget - resident:
+                    job = self.pending_builds.popleft()
+                    self._reject(job, MemoryError(
+                        f"build {job.name!r} needs about {job.footprint} bytes; the budget leaves "
+                        f"{self.budget - resident} beside the resident sets"))
                 # admit labeling jobs
                 admitted = admit_jobs(list(self.pending_builds), self.build_slots - self.running_builds,
                                       self.budget, self.used)
@@ -275,6 +369,8 @@ class LabelServer:
                     self.pending_builds.popleft()
                     self.used += job.footprint
                     self.running_builds += 1
+                    self.running_names.add(job.name)
+                    self.peak_used = max(self.peak_used, self.used)
                     self.pool.submit(self._run_build, job)
                 # coalesce ready query requests (their set must be resident)
                 batch = []
@@ -290,7 +386,9 @@ class LabelServer:
             if not progressed:
                 with self.wake:
                     if not self.stop_flag:
-                        self.wake.wait(timeout=2e-4)
+                        # launches in flight are polled (their CUDA events);
+                        # otherwise sleep until a submit or a build wakes us
+                        self.wake.wait(timeout=2e-4 if self.inflight else 0.05)
 
 
 def latency_summary(reqs: list) -> dict:

@@ -131,3 +131,40 @@ def test_rmat22_invariants_all_rows(rmat22):
             inc = hub[a + 1:b].long() > hub[a:b - 1].long()
             assert bool(torch.all(inc | ~same))              # strictly increasing within rows
         del q, r
+
+
+def test_rmat22_serving_results_identical_alone_and_in_the_mix(rmat22):
+    """The serving workload at full size: the R-MAT scale-22 labels resident,
+    labeling jobs of the batched workload's size distribution admitted
+    beside them, 300 requests of 1..65,536 uniform pairs (seed 4) arriving
+    while jobs build.  Every answer in the mix equals the same pairs answered
+    alone; the answers from three sources equal BFS distances."""
+    from paper_1906_12018_gb300.serve import LabelServer
+
+    g, order, lab = rmat22
+    srv = LabelServer(build_slots=2, max_inflight=2)
+    try:
+        srv.add_resident("base", lab)
+        for i in range(6):
+            s = G.small_graph(i)
+            srv.submit_build(f"job{i}", s.off, s.col, G.degree_order(s))
+        rng = np.random.default_rng(4)
+        reqs = [srv.submit_query("base", rng.integers(0, g.n, (int(rng.integers(1, 65537)), 2)).astype(np.int32))
+                for _ in range(300)]
+        srv.wait_idle()
+        allp = np.concatenate([r.pairs for r in reqs])
+        alone = gpu_query(lab, allp)
+        assert np.array_equal(np.concatenate([r.result for r in reqs]), alone)
+        srcs = rng.choice(g.n, 3, replace=False)
+        for s in srcs:
+            D = O.bfs(g.off, g.col, int(s))
+            tg = rng.integers(0, g.n, 2000).astype(np.int32)
+            pairs = np.stack([np.full(2000, s, np.int32), tg], 1)
+            assert np.array_equal(gpu_query(lab, pairs), D[tg])
+        assert len(srv.completed_builds) == 6
+    finally:
+        for nm in list(srv.sets):
+            if nm != "base":
+                srv.drop(nm)
+        srv.sets.pop("base", None)
+        srv.close()

@@ -9,6 +9,7 @@ from paper_1906_12018_gb300 import graphs as G
 from paper_1906_12018_gb300 import plb
 from paper_1906_12018_gb300.serve import LabelServer, latency_summary
 
+import oracle as O  # noqa: E402
 from gpu_util import gpu_build, gpu_query, host_labels
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +42,12 @@ def test_results_identical_alone_and_in_the_mix():
         for name, r in reqs:
             lab = srv.sets[name]
             assert np.array_equal(r.result, gpu_query(lab, r.pairs)), name
+        # and a sample of the mixed answers equals BFS distances
+        for name, r in [x for x in reqs if x[0] == "base"][:4]:
+            for s in np.unique(r.pairs[:, 0])[:5]:
+                D = O.bfs(base.off, base.col, int(s))
+                m = r.pairs[:, 0] == s
+                assert np.array_equal(r.result[m], D[r.pairs[m, 1]])
         st = latency_summary([r for _, r in reqs])
         assert st["requests"] == 60 and st["p99_ms"] >= st["p50_ms"] > 0
     finally:
@@ -65,3 +72,28 @@ def test_autotuned_options_keep_labels_identical(tmp_path, monkeypatch):
     for a, b in zip(tuned, plain):
         for x, y in zip(host_labels(a), host_labels(b)):
             assert np.array_equal(x, y)
+
+
+def test_admission_under_a_small_hbm_budget():
+    """A budget that holds about two build footprints beside the resident
+    set: jobs wait for memory, the admitted footprints never exceed the
+    budget, every job completes, and its labels equal a build run alone."""
+    from paper_1906_12018_gb300.serve import build_footprint
+
+    base = G.workload("rmat12")
+    jobs = [G.small_graph(i) for i in range(8)]
+    fps = [build_footprint(g.n, g.nnz) for g in jobs]
+    resident = gpu_build(base, G.degree_order(base))
+    budget = resident.nbytes() + int(2.2 * max(fps))
+    srv = LabelServer(hbm_budget=budget, build_slots=4, max_inflight=2)
+    try:
+        srv.add_resident("base", resident)
+        futs = [srv.submit_build(f"job{i}", g.off, g.col, G.degree_order(g)) for i, g in enumerate(jobs)]
+        srv.wait_idle()
+        assert srv.peak_used <= budget
+        for i, (g, f) in enumerate(zip(jobs, futs)):
+            alone = host_labels(gpu_build(g, G.degree_order(g)))
+            for a, b in zip(alone, host_labels(f.result())):
+                assert np.array_equal(a, b), i
+    finally:
+        srv.close()
