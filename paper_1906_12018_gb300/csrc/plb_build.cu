@@ -226,6 +226,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                                 (int)(16384 * sizeof(uint32_t))));
     // block tier: per-block buffer of accepted hubs (at most v < n per vertex)
     uint32_t* gacc = pool.alloc<uint32_t>((int64_t)grid_b * std::max<int64_t>(n, 1));
+    // per-vertex check records (row bounds and probe-table descriptor), packed before each gather
+    uint4* hrec = pool.alloc<uint4>(std::max<int64_t>(n, 1));
     PLB_ALLOC_OK();
 
     // ------------------------------------------------------------ rounds
@@ -253,6 +255,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.htab_h = htab;
         p.top = top;
         p.top_h = top;
+        p.hrec_h = hrec;
         p.gscratch = gacc;
         p.gscratch_words = std::max<int64_t>(n, 1);
         p.rbound = rbound;
@@ -297,6 +300,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
     } side_guard{side, ev_fork, ev_join};
     auto launch_gp = [&](GpParams p, cudaEvent_t* g1) -> cudaError_t {
+        k_pack_hrec<<<gflat, kFlatThreads, 0, s>>>(p.loff, hdesc, hrec, n, ctr);
+        st.launches += 1;
         GpParams w = p, b = p;
         w.list = R;  // warp tier
         w.list_n = &ctr->nR;

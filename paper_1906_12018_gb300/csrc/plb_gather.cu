@@ -15,7 +15,6 @@ namespace {
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 }  // namespace
 
-constexpr int kPrefilterMinItems = 12;  // prefilter only candidates with longer checks
 // Side B of the check (see check_chunk), per tier (measured: side B saves most
 // on power-law graphs with heavy hubs in both tiers).
 constexpr int kWarpSideBMin = 16, kWarpSideBShift = 1;
@@ -81,21 +80,41 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
     const int lane = threadIdx.x & 31;
     int64_t base = 0;  // A: start of L(h); B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
+    // h's check record (row bounds and probe-table descriptor: one 16-byte
+    // load, one memory sector) is requested before the top-hub prefilter
+    // reads h's masks, so the two loads overlap
+    uint4 rec = make_uint4(0u, 0u, 0u, 0u);
+    if (valid && p.hrec_h) rec = p.hrec_h[h];
+    // every candidate first tries the exact top-hub prefilter (one mask row
+    // per distance level; a hit settles the candidate without a scan)
+    const unsigned pf = top_prefilter(p.top_h, tv, d, h, valid);
+    if (lane == 0) prefiltered += __popc(pf);
+    const bool pruned = (pf >> lane) & 1u;
     if (valid) {
-        // the row bounds and the probe-table descriptor of h are loaded
-        // together (independent loads, one round trip)
-        const int64_t hb = p.loff_h[h];
-        const int64_t he = p.loff_h[h + 1];
-        const uint64_t hd = p.hdesc_h[h];
+        int64_t hb, he;
+        uint64_t hd;
+        if (p.hrec_h) {
+            const uint64_t row = ((uint64_t)rec.y << 32) | rec.x;
+            hb = (int64_t)(row >> 24);
+            he = hb + (int64_t)(row & 0xFFFFFFu);
+            hd = ((uint64_t)rec.w << 32) | rec.z;
+        } else if (!pruned || p.count_check) {
+            hb = p.loff_h[h];
+            he = p.loff_h[h + 1];
+            hd = p.hdesc_h[h];
+        } else {
+            hb = he = 0;
+            hd = 0;
+        }
         const int la = (int)(he - hb) - 1;
-        base = hb;
-        items = la;
         if (p.count_check) {  // the cost model's reads: L(v)'s entries below h, and L(h)
             chk[0] += (unsigned long long)lower_bound_u32(lv, lvlen, pack(h, 0));
             chk[1] += (unsigned long long)(la + 1);
         }
-        if (la >= b_min) {
-            if (hd) {
+        if (!pruned) {
+            base = hb;
+            items = la;
+            if (la >= b_min && hd) {
                 const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
                 if (mv_global ? lb < la : (lb << b_shift) < la) {
                     items = lb;
@@ -105,13 +124,7 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
             }
         }
     }
-    // candidates with a long check first try the top-hub prefilter
-    const unsigned pf = top_prefilter(p.top_h, tv, d, h, valid && items >= kPrefilterMinItems);
-    if (lane == 0) prefiltered += __popc(pf);
-    if ((pf >> lane) & 1u) {
-        valid = false;
-        items = 0;
-    }
+    if (pruned) valid = false;
     const unsigned vmask = __ballot_sync(kFull, valid);
     const int incl = warp_incl_scan(items, lane);
     const int total = __shfl_sync(kFull, incl, 31);
@@ -804,6 +817,19 @@ __global__ void __launch_bounds__(256, 3) k_gp_block(GpParams p) {
         atomicAdd(&p.ctr->staged, cnt[3]);
         atomicAdd(&p.ctr->accepted, cnt[5]);
         atomicAdd(&p.ctr->tier[1], cnt[6]);
+    }
+}
+
+// Check records of all rows, from the label offsets and the probe index as
+// they stand for the coming gather (a finished round returns at once).
+__global__ void k_pack_hrec(const int64_t* loff, const uint64_t* hdesc, uint4* hrec, int64_t n,
+                            const RoundCounters* ctr) {
+    if (ctr->done) return;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = loff[v];
+        const uint64_t row = hrec_row((uint64_t)a, (uint64_t)(loff[v + 1] - a));
+        const uint64_t hd = hdesc[v];
+        hrec[v] = make_uint4((uint32_t)row, (uint32_t)(row >> 32), (uint32_t)hd, (uint32_t)(hd >> 32));
     }
 }
 

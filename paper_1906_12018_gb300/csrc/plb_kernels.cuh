@@ -95,6 +95,8 @@ struct GpParams {
     const uint64_t* hdesc_h;
     const uint32_t* htab_h;
     const uint32_t* top_h;
+    const uint4* hrec_h;       // per vertex of the candidates' side, or null: {row start << 24 | row length
+                               // (64 bits), probe-table descriptor (64 bits)}, one 16-byte load per check
     const uint32_t* rbound;    // per receiver: candidate bound min(v, messages)
     const int64_t* ostart;     // per receiver: start of its new frontier row (the scan of the bounds),
                                // or null (rows reserved with an atomic cursor)
@@ -147,6 +149,12 @@ constexpr int kIndexMinLen = 16;
 // the rows are short, 2048 when they are long.
 constexpr int kIndexWarps = 8;
 constexpr int kIndexSmemSlotsMax = 2048;
+
+// Check records (GpParams::hrec_h): row start << 24 | length, then the
+// probe-table descriptor.
+__host__ __device__ __forceinline__ uint64_t hrec_row(uint64_t start, uint64_t len) { return (start << 24) | len; }
+__global__ void k_pack_hrec(const int64_t* loff, const uint64_t* hdesc, uint4* hrec, int64_t n,
+                            const RoundCounters* ctr);
 
 // Routing limits of k_collect (see the tier geometry in build_core).
 struct TierLimits {
