@@ -300,7 +300,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         }
     } side_guard{side, ev_fork, ev_join};
     auto launch_gp = [&](GpParams p, cudaEvent_t* g1) -> cudaError_t {
-        k_pack_hrec<<<gflat, kFlatThreads, 0, s>>>(p.loff, hdesc, hrec, n, ctr);
+        k_pack_hrec<<<gflat, kFlatThreads, 0, s>>>(p.loff, p.lent, hdesc, hrec, n, ctr);
         st.launches += 1;
         GpParams w = p, b = p;
         w.list = R;  // warp tier

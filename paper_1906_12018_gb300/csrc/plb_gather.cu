@@ -71,15 +71,21 @@ __device__ __forceinline__ void stage_exact_levels(const uint32_t* top, int32_t 
 // a factor 2^b_shift against a shared-memory M (whose probes are cheaper
 // than the global table's).  All (candidate, entry) pairs are spread over
 // the lanes; a candidate's remaining entries are skipped once it has a
-// witness.  Returns the lanes whose candidate survives.
+// witness.  Every candidate first goes through the top-hub prefilter, which
+// is exact for the kTopHubs highest-ranked hubs while d <= kTopLevels + 1
+// (a witness w has 1 <= d(w,v), d(w,h) <= d - 1): for a candidate it does not
+// prune, no top hub is a witness, so both scans start past the top hubs
+// (L(h)'s count of them comes with h's check record, L(v)'s is tv_top).
+// Returns the lanes whose candidate survives.
 __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, const uint32_t* M, int log_m,
                                                 bool mv_global, int b_min, int b_shift, const uint32_t* lv,
-                                                int64_t lvlen, uint32_t h, bool valid, unsigned long long& probed,
-                                                const uint32_t* tv, unsigned long long& prefiltered,
-                                                unsigned long long* chk) {
+                                                int64_t lvlen, int tv_top, uint32_t h, bool valid,
+                                                unsigned long long& probed, const uint32_t* tv,
+                                                unsigned long long& prefiltered, unsigned long long* chk) {
     const int lane = threadIdx.x & 31;
-    int64_t base = 0;  // A: start of L(h); B: start of h's probe table
+    int64_t base = 0;  // A: first entry of L(h) scanned; B: start of h's probe table
     int items = 0, meta = 0;  // meta: 0 = side A, else log2(table size) + 1
+    int skip_b = 0;           // side B: the scan of L(v) starts at this entry
     // h's check record (row bounds and probe-table descriptor: one 16-byte
     // load, one memory sector) is requested before the top-hub prefilter
     // reads h's masks, so the two loads overlap
@@ -90,14 +96,18 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
     const unsigned pf = top_prefilter(p.top_h, tv, d, h, valid);
     if (lane == 0) prefiltered += __popc(pf);
     const bool pruned = (pf >> lane) & 1u;
+    // past the top hubs when the prefilter settles them (see above)
+    const bool skip_top = d <= (uint32_t)kTopLevels + 1u;
     if (valid) {
         int64_t hb, he;
         uint64_t hd;
+        int top_h = 0;  // entries of L(h) with hub < kTopHubs
         if (p.hrec_h) {
             const uint64_t row = ((uint64_t)rec.y << 32) | rec.x;
             hb = (int64_t)(row >> 24);
             he = hb + (int64_t)(row & 0xFFFFFFu);
-            hd = ((uint64_t)rec.w << 32) | rec.z;
+            hd = (((uint64_t)rec.w << 32) | rec.z) & kHrecDescMask;
+            top_h = (int)(rec.w >> kHrecTopShift);
         } else if (!pruned || p.count_check) {
             hb = p.loff_h[h];
             he = p.loff_h[h + 1];
@@ -112,14 +122,17 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
             chk[1] += (unsigned long long)(la + 1);
         }
         if (!pruned) {
-            base = hb;
-            items = la;
+            const int sa = skip_top ? min(top_h, la) : 0;  // side A starts past L(h)'s top hubs
+            base = hb + sa;
+            items = la - sa;
             if (la >= b_min && hd) {
                 const int lb = (int)lower_bound_u32(lv, lvlen, pack(h, 0));
-                if (mv_global ? lb < la : (lb << b_shift) < la) {
-                    items = lb;
+                const int sb = skip_top ? min(tv_top, lb) : 0;  // side B starts past L(v)'s top hubs
+                if (mv_global ? lb - sb < la - sa : ((lb - sb) << b_shift) < la - sa) {
+                    items = lb - sb;
                     base = (int64_t)(hd >> 8);
                     meta = (int)(hd & 0xFFu) + 1;  // log2 + 1
+                    skip_b = sb;
                 }
             }
         }
@@ -144,9 +157,10 @@ __device__ __forceinline__ unsigned check_chunk(const GpParams& p, uint32_t d, c
             bku[u] = __shfl_sync(kFull, base, k);
             const int exk = __shfl_sync(kFull, excl, k);
             mku[u] = __shfl_sync(kFull, meta, k);
+            const int sbk = __shfl_sync(kFull, skip_b, k);
             ku[u] = (it < total && !((pm >> k) & 1u)) ? k : -1;
             xu[u] = kEmpty;
-            if (ku[u] >= 0) xu[u] = mku[u] == 0 ? p.lent_h[bku[u] + (it - exk)] : lv[it - exk];
+            if (ku[u] >= 0) xu[u] = mku[u] == 0 ? p.lent_h[bku[u] + (it - exk)] : lv[sbk + (it - exk)];
         }
         unsigned hits = 0;
 #pragma unroll
@@ -199,13 +213,23 @@ __device__ __forceinline__ bool gather_range(const GpParams& p, int64_t nb, int6
         msgs += (lane == 0) ? (unsigned long long)total : 0ull;
         for (int ib = 0; ib < total; ib += 32 * kGatherUnroll) {
             uint32_t hv[kGatherUnroll];
+            // a step inside one row (long rows): every lane reads that row,
+            // no per-lane owner search
+            const int k1 = warp_owner(excl, ib);
+            const int end1 = k1 < 31 ? __shfl_sync(kFull, excl, k1 + 1) : total;
+            if (ib + 32 * kGatherUnroll <= end1) {
+                const int64_t at = __shfl_sync(kFull, st, k1) + (ib - __shfl_sync(kFull, excl, k1)) + lane;
 #pragma unroll
-            for (int u = 0; u < kGatherUnroll; ++u) {
-                const int it = ib + 32 * u + lane;
-                const int k = warp_owner(excl, it);
-                const int64_t stk = __shfl_sync(kFull, st, k);
-                const int exk = __shfl_sync(kFull, excl, k);
-                hv[u] = it < total ? p.fhub[stk + (it - exk)] : kEmpty;
+                for (int u = 0; u < kGatherUnroll; ++u) hv[u] = p.fhub[at + 32 * u];
+            } else {
+#pragma unroll
+                for (int u = 0; u < kGatherUnroll; ++u) {
+                    const int it = ib + 32 * u + lane;
+                    const int k = warp_owner(excl, it);
+                    const int64_t stk = __shfl_sync(kFull, st, k);
+                    const int exk = __shfl_sync(kFull, excl, k);
+                    hv[u] = it < total ? p.fhub[stk + (it - exk)] : kEmpty;
+                }
             }
             int nins = 0;
 #pragma unroll
@@ -372,13 +396,23 @@ __device__ void gather_block(const GpParams& p, int64_t nb, int64_t ne, uint32_t
                     const int wend_w = min(wend, wcap);
                     for (int ib = it0; ib < wend_w; ib += 32 * kGatherUnroll) {
                         uint32_t hv[kGatherUnroll];
+                        // a step inside one row (long rows): every lane reads
+                        // that row, no per-lane owner search
+                        const int k1 = warp_owner(ex, ib);
+                        const int end1 = k1 < 31 ? __shfl_sync(kFull, ex, k1 + 1) : wcap;
+                        if (ib + 32 * kGatherUnroll <= min(end1, wend_w)) {
+                            const int64_t at = __shfl_sync(kFull, stv, k1) + (ib - __shfl_sync(kFull, ex, k1)) + lane;
 #pragma unroll
-                        for (int u = 0; u < kGatherUnroll; ++u) {
-                            const int it = ib + 32 * u + lane;
-                            const int kk = warp_owner(ex, it);
-                            const int exk = __shfl_sync(kFull, ex, kk);
-                            const int64_t stk = __shfl_sync(kFull, stv, kk);
-                            hv[u] = it < wend_w ? p.fhub[stk + (it - exk)] : kEmpty;
+                            for (int u = 0; u < kGatherUnroll; ++u) hv[u] = p.fhub[at + 32 * u];
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < kGatherUnroll; ++u) {
+                                const int it = ib + 32 * u + lane;
+                                const int kk = warp_owner(ex, it);
+                                const int exk = __shfl_sync(kFull, ex, kk);
+                                const int64_t stk = __shfl_sync(kFull, stv, kk);
+                                hv[u] = it < wend_w ? p.fhub[stk + (it - exk)] : kEmpty;
+                            }
                         }
                         int nins = 0;
 #pragma unroll
@@ -505,6 +539,8 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             for (int64_t j = lane; j < ll; j += 32) lvs[j] = p.lent[lb + j];
             lvp = lvs;
         }
+        // entries of L(v) with hub below kTopHubs (the checks' side B starts past them)
+        const int lv_top = nc > 0 ? (int)lower_bound_u32(lvp, ll, pack((uint32_t)kTopHubs, 0)) : 0;
         // distance checks, 32 candidates at a time; survivors compacted in place
         uint32_t* tv = tvs + wib * kTopRow;
         if (nc > 0) stage_exact_levels(p.top, v, tv, lane, 32);
@@ -514,8 +550,8 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
             const bool valid = cb + lane < nc;
             const uint32_t h = valid ? S[cb + lane] : 0u;
             __syncwarp();
-            const unsigned okm = check_chunk(p, d, Mv, log_m, mglob, kWarpSideBMin, kWarpSideBShift, lvp, ll, h,
-                                             valid, c_probed, tv, c_pref, c_chk);
+            const unsigned okm = check_chunk(p, d, Mv, log_m, mglob, kWarpSideBMin, kWarpSideBShift, lvp, ll, lv_top,
+                                             h, valid, c_probed, tv, c_pref, c_chk);
             if ((okm >> lane) & 1u) S[nacc + __popc(okm & ((1u << lane) - 1u))] = h;
             nacc += __popc(okm);
             __syncwarp();
@@ -680,6 +716,8 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
             lvp = lvs;
         }
         __syncthreads();
+        // entries of L(v) with hub below kTopHubs (the checks' side B starts past them)
+        const int lv_top = (int)lower_bound_u32(lvp, ll, pack((uint32_t)kTopHubs, 0));
         const int nc_set = min(*(volatile int*)&sh[SH_NC], limit);  // candidates from the set
         if (tid == 0) cnt[2] += nc_set;
         if (lo < W) {
@@ -705,7 +743,7 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
                 for (int cb = 0; cb < nchk; cb += 32) {
                     const uint32_t h = stage[cb + lane];
                     const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lvp,
-                                                     ll, h, true, cnt[4], tv, cnt[7], cnt + 8);
+                                                     ll, lv_top, h, true, cnt[4], tv, cnt[7], cnt + 8);
                     int base = 0;
                     if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
                     base = __shfl_sync(kFull, base, 0);
@@ -740,8 +778,8 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
                 if (lane == 0) cnt[2] -= __popc(km);
                 if (known) valid = false;
             }
-            const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lvp, ll, h,
-                                             valid, cnt[4], tv, cnt[7], cnt + 8);
+            const unsigned okm = check_chunk(p, d, Mp, log_mp, !useM, kBlockSideBMin, kBlockSideBShift, lvp, ll,
+                                             lv_top, h, valid, cnt[4], tv, cnt[7], cnt + 8);
             int base = 0;
             if (lane == 0 && okm) base = atomicAdd(&sh[SH_ACC], __popc(okm));
             base = __shfl_sync(kFull, base, 0);
@@ -822,13 +860,15 @@ __global__ void __launch_bounds__(256, 3) k_gp_block(GpParams p) {
 
 // Check records of all rows, from the label offsets and the probe index as
 // they stand for the coming gather (a finished round returns at once).
-__global__ void k_pack_hrec(const int64_t* loff, const uint64_t* hdesc, uint4* hrec, int64_t n,
+__global__ void k_pack_hrec(const int64_t* loff, const uint32_t* lent, const uint64_t* hdesc, uint4* hrec, int64_t n,
                             const RoundCounters* ctr) {
     if (ctr->done) return;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = loff[v];
-        const uint64_t row = hrec_row((uint64_t)a, (uint64_t)(loff[v + 1] - a));
-        const uint64_t hd = hdesc[v];
+        const int64_t a = loff[v], len = loff[v + 1] - a;
+        const uint64_t row = hrec_row((uint64_t)a, (uint64_t)len);
+        // entries of L(v) with hub < kTopHubs (rows are hub-sorted)
+        const uint64_t top = (uint64_t)lower_bound_u32(lent + a, len, pack((uint32_t)kTopHubs, 0));
+        const uint64_t hd = hdesc[v] | (top << (32 + kHrecTopShift));
         hrec[v] = make_uint4((uint32_t)row, (uint32_t)(row >> 32), (uint32_t)hd, (uint32_t)(hd >> 32));
     }
 }

@@ -151,9 +151,12 @@ constexpr int kIndexWarps = 8;
 constexpr int kIndexSmemSlotsMax = 2048;
 
 // Check records (GpParams::hrec_h): row start << 24 | length, then the
-// probe-table descriptor.
+// probe-table descriptor (table start << 8 | log2 slots, below 2^48) with the
+// row's count of entries whose hub is below kTopHubs in its top 16 bits.
 __host__ __device__ __forceinline__ uint64_t hrec_row(uint64_t start, uint64_t len) { return (start << 24) | len; }
-__global__ void k_pack_hrec(const int64_t* loff, const uint64_t* hdesc, uint4* hrec, int64_t n,
+constexpr int kHrecTopShift = 16;  // within the record's last word
+constexpr uint64_t kHrecDescMask = (uint64_t(1) << 48) - 1;
+__global__ void k_pack_hrec(const int64_t* loff, const uint32_t* lent, const uint64_t* hdesc, uint4* hrec, int64_t n,
                             const RoundCounters* ctr);
 
 // Routing limits of k_collect (see the tier geometry in build_core).
