@@ -873,27 +873,34 @@ def measure_build(args, g, order, dev, steps: int, warmup: int, e2e_steps: int, 
         h_hub = torch.empty(n_labels, dtype=torch.int32, pin_memory=True)
         h_dist = torch.empty(n_labels, dtype=torch.uint8, pin_memory=True)
         d2h = h_off.numel() * 8 + h_hub.numel() * 4 + h_dist.numel()
-        e2e_ms = []
+        e2e_ms, phases = [], []
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         for k in range(e2e_steps + 1):  # the first iteration is a warm-up
             flush.zero_()
             torch.cuda.synchronize(dev)
             t = time.perf_counter()
+            ev[0].record(stream)
             d_rp = h_rp.to(dev, non_blocking=True)
             d_col = h_col.to(dev, non_blocking=True)
             d_o = h_o.to(dev, non_blocking=True)
+            ev[1].record(stream)
             lab = plb.build(d_rp, d_col, d_o, opts)
+            ev[2].record(stream)
             off_d, hub_d, dist_d = lab.device_arrays()
             h_off.copy_(off_d, non_blocking=True)
             h_hub.copy_(hub_d, non_blocking=True)
             h_dist.copy_(dist_d, non_blocking=True)
+            ev[3].record(stream)
             torch.cuda.synchronize(dev)
             if k > 0:
                 e2e_ms.append(1e3 * (time.perf_counter() - t))
+                phases.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
             lab.free()
             del d_rp, d_col, d_o
         e2e_ms_med = max_over_ranks(statistics.median(e2e_ms), world)
         e2e = {"value": whole_job_rate(g.m, e2e_ms_med, world), "unit": "edges/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_med}
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_med,
+               "phases_ms": {k: statistics.median(x[i] for x in phases) for i, k in enumerate(("h2d", "build", "d2h"))}}
         del h_off, h_hub, h_dist
     del flush, rp, col, o
     plb.release_cached_memory()
