@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(256, 3) k_gp_warp(GpParams p) {
 }
 
 // Block-per-vertex scalars in shared memory (ints)
-enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_HI = 4, SH_TMP = 5, SH_START = 6 /* 2 ints */,
+enum { SH_UNIQ = 0, SH_OVF = 1, SH_ACC = 2, SH_NC = 3, SH_HI = 4, SH_TMP = 5, SH_START = 6 /* 2 ints */, SH_NEXT = 8,
        SH_WORDS = 48 };
 
 // One block per vertex, any size.  The candidates are processed in passes
@@ -678,6 +678,7 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
             sh[SH_OVF] = 0;
             sh[SH_ACC] = 0;
             sh[SH_NC] = 0;
+            sh[SH_NEXT] = 0;
             *hi_sm = (uint32_t)min((int64_t)v, (int64_t)lo + width);
         }
         __syncthreads();
@@ -764,10 +765,15 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
             __syncthreads();
         }
         // distance checks of C (the set's candidates, then the byte map's
-        // remainders): warp w takes candidate chunks w, w + nw, ...; the
-        // survivors are appended (unsorted) to this block's scratch
+        // remainders): each warp takes the next chunk of 32 from a shared
+        // counter (chunks differ in cost); the survivors are appended
+        // (unsorted) to this block's scratch
         const int nc = *(volatile int*)&sh[SH_NC];
-        for (int cb = 32 * wid; cb < nc; cb += 32 * nw) {
+        for (;;) {
+            int cb = 0;
+            if (lane == 0) cb = atomicAdd(&sh[SH_NEXT], 32);
+            cb = __shfl_sync(kFull, cb, 0);
+            if (cb >= nc) break;
             bool valid = cb + lane < nc;
             const uint32_t h = valid ? C[cb + lane] : 0u;
             // without the map, set candidates may be hubs of v already (they
