@@ -668,7 +668,7 @@ __device__ void gp_block_vertex(const GpParams& p, uint32_t d, int32_t v, uint32
     // hubs below W (the most frequent messages) are deduplicated in the byte
     // map, in the first pass, for vertices with many messages (for the others
     // clearing and scanning the map costs more than the hashing it saves)
-    const uint32_t W = p.rbound[v] >= (uint32_t)(kByteHubs / 4) ? min((uint32_t)kByteHubs, (uint32_t)v) : 0u;
+    const uint32_t W = p.rbound[v] >= kByteMinBound ? min((uint32_t)kByteHubs, (uint32_t)v) : 0u;
     const int nbw = (int)((W + 3) / 4);  // byte-map words in use
     for (int q = tid; q < nbw; q += nthr) reinterpret_cast<uint32_t*>(B)[q] = 0u;
     while ((int64_t)lo < (int64_t)v) {

@@ -138,7 +138,10 @@ constexpr int kCheckUnroll = 2;
 
 // Block tier: hubs below this rank are deduplicated in a shared-memory byte
 // map (one byte per hub) instead of the hash set.
-constexpr int kByteHubs = 8192;
+constexpr int kByteHubs = 24576;
+// Receivers whose candidate bound reaches this use the byte map (for fewer
+// candidates clearing and scanning it costs more than the hashing it saves).
+constexpr uint32_t kByteMinBound = 2048;
 constexpr int kByteStage = 160;  // per-warp staging of byte-map candidates (< 32 carried + 128 new)
 
 // Rows of L with at least this many entries get a hub-keyed probe table.
