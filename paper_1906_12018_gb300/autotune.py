@@ -29,7 +29,7 @@ SPACE = {
     "warp_label_cap": [256, 512, 1024],
     "block_threads": [128, 256],
     "block_cand_cap": [1024, 2048, 4096],
-    "block_label_cap": [1024, 2048],
+    "block_label_cap": [512, 1024],
 }
 
 

@@ -114,7 +114,7 @@ void plb_default_options(plb_options* o) {
     o->validate = 1;
     o->warp_label_cap = 512;
     o->warp_cand_cap = 512;
-    o->block_label_cap = 1024;
+    o->block_label_cap = 512;
     o->block_cand_cap = 2048;
     o->block_threads = 256;
     o->use_graph = 0;

@@ -138,7 +138,7 @@ constexpr int kCheckUnroll = 2;
 
 // Block tier: hubs below this rank are deduplicated in a shared-memory byte
 // map (one byte per hub) instead of the hash set.
-constexpr int kByteHubs = 24576;
+constexpr int kByteHubs = 32768;
 // Receivers whose candidate bound reaches this use the byte map (for fewer
 // candidates clearing and scanning it costs more than the hashing it saves).
 constexpr uint32_t kByteMinBound = 2048;
