@@ -197,12 +197,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                                                                            block_cand + (int64_t)kGatherUnroll * bthr),
                                                           (int64_t)kByteStage * (bthr / 32)));
     const int b_log_m = ceil_log2_i64(2 * (int64_t)std::max(o.block_label_cap, 64) + 2 * bthr);
-    // scalars (48) + warp sums (34) + histogram (256) + top-hub masks + prefix per thread + 64-bit row
-    // start per thread + set (also kByteStage per warp of byte-map staging) + map + candidate list
-    // (limit + 32 per warp) + byte map
-    const size_t b_smem = sizeof(uint32_t) * (48 + 34 + 256 + kTopRow + (size_t)((bthr + 2) & ~1) + 2 * (size_t)bthr +
-                                              (size_t)(1 << b_log_s) + (size_t)(1 << b_log_m) +
-                                              (size_t)(block_cand + bthr) + kByteHubs / 4);
+    const size_t b_smem = gp_block_smem_bytes(bthr, b_log_s, b_log_m, block_cand);
     TierLimits lim;
     lim.warp_bound = 2 * (int64_t)warp_cand;
     lim.warp_label = warp_label;

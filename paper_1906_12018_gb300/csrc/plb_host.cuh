@@ -102,6 +102,17 @@ inline int pow2_at_least(int64_t x) {
     return p;
 }
 
+// Dynamic shared memory of k_gp_block in bytes, in the order the kernel
+// carves it up: scalars (48 words) + warp sums (34) + histogram (256) +
+// top-hub masks + prefix per thread + 64-bit row start per thread + set (also
+// kByteStage per warp of byte-map staging) + map + candidate list (limit +
+// 32 per warp) + byte map.
+inline size_t gp_block_smem_bytes(int bthr, int log_s, int log_m, int cand_limit) {
+    return sizeof(uint32_t) * (48 + 34 + 256 + kTopRow + (size_t)((bthr + 2) & ~1) + 2 * (size_t)bthr +
+                               ((size_t)1 << log_s) + ((size_t)1 << log_m) + (size_t)cand_limit + (size_t)bthr +
+                               kByteHubs / 4);
+}
+
 // Records the failing CUDA call for plb_last_error (this thread).
 void set_last_error(cudaError_t e, int line);
 
