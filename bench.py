@@ -802,9 +802,20 @@ def measure_build(args, g, order, dev, steps: int, warmup: int, e2e_steps: int, 
     ms_max = max_over_ranks(ms, world)
     launches = st0["launches"] * steps
 
-    # kernel-class timings and counters: one profiled build
+    # kernel-class timings and counters: one profiled build; around it the
+    # high mark of the library's memory pool (the build's device memory
+    # beyond the caller's CSR, against the serving loop's footprint model)
+    from paper_1906_12018_gb300.serve import build_footprint
+
+    torch.cuda.synchronize(dev)
+    mem0 = plb.memory_stats(reset=True)
     lab = plb.build(rp, col, o, plb.default_options(profile=1, batch_hubs=args.batch_hubs))
     st = lab.stats()
+    torch.cuda.synchronize(dev)
+    mem1 = plb.memory_stats()
+    in_bytes = rp.numel() * 8 + col.numel() * 4 + o.numel() * 4
+    memory = {"build_peak_bytes": mem1["used_high"] - mem0["used"], "labels_bytes": lab.nbytes(),
+              "footprint_model_bytes": build_footprint(g.n, g.nnz) - in_bytes, "input_bytes": in_bytes}
     gp_ms = sum(st["ms_gather_prune"])
     ab = algorithmic_bytes(st, g.n)
     # round 1: k_round1_count and k_round1; every later host-driven round: the
@@ -906,7 +917,7 @@ def measure_build(args, g, order, dev, steps: int, warmup: int, e2e_steps: int, 
     plb.release_cached_memory()
     torch.cuda.empty_cache()
     return {"ms": ms, "ms_max": ms_max, "n_labels": n_labels, "rounds": st0["rounds"], "launches": launches,
-            "wall": wall, "clocks": clk.summary(), "roofline": roof, "e2e": e2e,
+            "wall": wall, "clocks": clk.summary(), "roofline": roof, "e2e": e2e, "memory": memory,
             "kernel_ms": {"prepare": st["ms_prepare"], "frontier": st["ms_frontier"],
                           "gather_prune": st["ms_gather_prune"][:2], "merge_sort_index": st["ms_merge"],
                           "finalize": st["ms_finalize"]},
@@ -1021,6 +1032,7 @@ def main():
             "counters": res["counters"],
             "e2e": res["e2e"],
             "queries": res["queries"],
+            "memory": res["memory"],
             "gpu_launches": res["launches"],
             "clocks": res["clocks"],
             "wall_s_timed": res["wall"],

@@ -242,6 +242,16 @@ int plb_labels_free(plb_labels* labels);
  * currently unused block to the driver (synchronises the device). */
 int plb_release_cached_memory(void);
 
+/* Device memory of the library's pool on the current device, in bytes:
+ * out[0] in use now, out[1] the most in use at once since the last reset,
+ * out[2] reserved from the driver now, out[3] the most reserved at once.
+ * out: host int64[4] (caller-owned).  reset != 0 then restarts both high
+ * marks from the current values (a build's peak is out[1] read after it
+ * with a reset before it).  Returns PLB_ERR_INVALID for a NULL out,
+ * PLB_ERR_CUDA when the pool cannot be queried; all zeros before the
+ * library's first allocation on the device. */
+int plb_memory_stats(int64_t* out, int reset);
+
 /* Degree order (Sec. 6.1: vertices ordered by degree): order_out (device,
  * int32[n]) receives rank -> id, degree descending, ties by smaller id.
  * Only row_ptr is read.  Allocates device scratch (8 bytes per vertex,

@@ -370,14 +370,18 @@ int plb_labels_free(plb_labels* L) {
         auto* sh = static_cast<plb::Shared*>(L->shared);
         if (--sh->refs == 0) {
             for (void* p : sh->ptrs)
-                if (p) cudaFree(p);
+                if (p) cudaFreeAsync(p, 0);
             delete sh;
         }
     } else {
         for (void* p : {(void*)L->off, (void*)L->packed, (void*)L->hub, (void*)L->dist, (void*)L->order})
-            if (p) cudaFree(p);
+            if (p) cudaFreeAsync(p, 0);
     }
     delete L;
+    // the blocks came from the library's stream-ordered pool: freed in stream
+    // order they return to it for the next build (its use counts drop), and
+    // the frees have completed when this returns
+    cudaDeviceSynchronize();
     return cudaGetLastError() == cudaSuccess ? PLB_OK : PLB_ERR_CUDA;
 }
 

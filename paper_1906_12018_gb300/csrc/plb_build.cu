@@ -147,17 +147,33 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     // shared-memory table buffer of the index kernels: 512 slots while the mean
     // row is short (most tables fit and eight blocks share an SM), else 2048
     auto index_slots = [&](int64_t total) { return total <= 128 * n ? 512 : kIndexSmemSlotsMax; };
-    auto build_index = [&](int which, int64_t total) -> int {
-        // packed tables take at most 4 |L| slots; keep as much again for growth
-        const int64_t want = 8 * total + 1024;
-        if (hcap < 6 * total + 1024) {
+    // Table pool size.  roomy: from the bound (packed tables take at most
+    // 4 |L| slots; as much again for growth), for graph segments whose rounds
+    // all update the index in place.  Otherwise from the packed tables' exact
+    // slot count (hoff[n], read back), with half as much again for the
+    // in-place updates of the following rounds; a pool that still overflows
+    // is repacked before the next gather.
+    auto build_index = [&](int which, int64_t total, bool roomy) -> int {
+        k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[which], n, tmp64, ctr);
+        if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
+        int64_t need = 6 * total + 1024, want = 8 * total + 1024;
+        if (!roomy) {
+            int64_t packed = 0;
+            int done = 0;
+            if (cudaMemcpyAsync(&packed, hoff + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaMemcpyAsync(&done, &ctr->done, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return PLB_ERR_CUDA;
+            if (done) return PLB_OK;  // a finished build: the index kernels would return at once
+            need = packed + 1024;
+            want = packed + packed / 2 + 1024;
+        }
+        if (hcap < need || (!roomy && hcap > 2 * want)) {
             pool.release(htab);
             hcap = want;
             htab = pool.alloc<uint32_t>(hcap);
             if (pool.failed) return PLB_ERR_OOM;
         }
-        k_index_size<<<gflat, kFlatThreads, 0, s>>>(loff[which], n, tmp64, ctr);
-        if (exclusive_scan_i64(tmp64, hoff, n, scan_scr, s) != cudaSuccess) return PLB_ERR_CUDA;
         const int slots = index_slots(total);
         k_index_build<<<grid_for((n + 255) / 256, 1, flat_grid_cap), kIndexWarps * 32,
                         sizeof(uint32_t) * kIndexWarps * slots, s>>>(loff[which], lent[which], hoff, htab, hdesc, n,
@@ -176,7 +192,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         return cudaGetLastError();
     };
     {
-        const int e = build_index(0, T);
+        const int e = build_index(0, T, false);
         if (e != PLB_OK) return e;
     }
     if (tm.on) tm.span(T_PREP, t0, tm.mark());
@@ -405,12 +421,16 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             PLB_CK(cudaMemcpyAsync(hctr, ctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
             PLB_CK(cudaStreamSynchronize(s));
             if (hctr->hovf) {  // the last update did not fit the table pool: rebuild it, packed
-                const int e = build_index(cur, T);
+                const int e = build_index(cur, T, false);
                 if (e != PLB_OK) return e;
             }
+            // (up to 2^31 entries: past that the buffer holds twice the last
+            // round's acceptance, set after the merge, and a round that still
+            // overflows it runs again; the bound far exceeds the acceptance of
+            // the rounds after the largest)
             if ((int64_t)hctr->bound_sum > fcap[nxt]) {
                 const int64_t want = std::min<int64_t>((int64_t)hctr->bound_sum + 1024,
-                                                       std::max<int64_t>(int64_t(1) << 31, 2 * fcap[nxt]));
+                                                       std::max<int64_t>(int64_t(1) << 31, fcap[nxt]));
                 if (want > fcap[nxt]) {
                     pool.release(fhub[nxt]);
                     fcap[nxt] = want;
@@ -493,7 +513,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
             // most rows reach kIndexMinLen in round 1, and a round that more
             // than doubles the labels outgrows most tables: a packed rebuild
             // (cheaper than a new table per row from the shared pool cursor)
-            const int e = build_index(cur, T);
+            const int e = build_index(cur, T, false);
             if (e != PLB_OK) return e;
         } else {
             PLB_CK(update_index(cur, T));  // a table that did not fit shows up as hovf at the next sync
@@ -557,7 +577,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                 if (!grow(lent[cur], lcap[cur], lc, T) || !grow(lent[cur ^ 1], lcap[cur ^ 1], lc, 0))
                     return PLB_ERR_OOM;
                 {
-                    const int e = build_index(cur, T);  // packed, with room for the segment's updates
+                    const int e = build_index(cur, T, true);  // packed, with room for the segment's updates
                     if (e != PLB_OK) return e;
                 }
                 PLB_CK(cudaStreamSynchronize(s));
@@ -696,7 +716,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
                 cur = nxt;
                 d = dd;
                 {
-                    const int e = build_index(cur, T);
+                    const int e = build_index(cur, T, true);
                     if (e != PLB_OK) return e;
                 }
                 PLB_CK(cudaMemsetAsync(ctr, 0, offsetof(RoundCounters, nA), s));
@@ -740,6 +760,11 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     if (status != PLB_OK) return status;
 
     // ------------------------------------------------------------ finalize
+    // only the final rows (loff, lent), the rank inverse, the scan buffers and
+    // the counters are read from here on: the round buffers (probe index,
+    // frontiers, tier scratch, masks, rank-space CSR) go back to the pool
+    // before the label set is allocated, which lowers the build's peak
+    pool.release_all_except({loff[cur], lent[cur], inv, tmp64, scan_scr, ctr});
     cudaEvent_t f0 = tm.on ? tm.mark() : nullptr;
     plb_labels* L = new plb_labels();
     L->n = n;

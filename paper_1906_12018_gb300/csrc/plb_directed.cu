@@ -491,6 +491,9 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
     if (status != PLB_OK) return status;
 
     // ------------------------------------------------------------ finalize
+    // the round buffers go back to the pool before the label sets are allocated
+    pool.release_all_except({side[0].loff[side[0].cur], side[0].lent[side[0].cur], side[1].loff[side[1].cur],
+                             side[1].lent[side[1].cur], side[0].ctr, side[1].ctr, inv, tmp64, scan_scr});
     cudaEvent_t f0 = tm.on ? tm.mark() : nullptr;
     plb_labels* Lk[2] = {nullptr, nullptr};
     auto fail = [&](int code) {

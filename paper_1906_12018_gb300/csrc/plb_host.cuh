@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstddef>
 #include <cstdio>
+#include <initializer_list>
 #include <vector>
 
 #include "plb_round.cuh"
@@ -41,6 +42,15 @@ struct DevPool {
             cudaFreeAsync(p, s);
             ptrs.erase(it);
         }
+    }
+    // Frees every allocation except those in keep (stream-ordered).
+    void release_all_except(std::initializer_list<const void*> keep) {
+        std::vector<void*> kept;
+        for (void* p : ptrs) {
+            if (std::find(keep.begin(), keep.end(), p) != keep.end()) kept.push_back(p);
+            else cudaFreeAsync(p, s);
+        }
+        ptrs.swap(kept);
     }
     ~DevPool() {
         for (void* p : ptrs) cudaFreeAsync(p, s);

@@ -59,3 +59,35 @@ extern "C" int plb_release_cached_memory(void) {
         }
     return PLB_OK;
 }
+
+extern "C" int plb_memory_stats(int64_t* out, int reset) {
+    if (!out) return PLB_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= plb::kMaxDevices) {
+        (void)cudaGetLastError();
+        return PLB_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(plb::g_pool_mu);
+    cudaMemPool_t pool = plb::g_pools[dev];
+    for (int i = 0; i < 4; ++i) out[i] = 0;
+    if (!pool) return PLB_OK;
+    const cudaMemPoolAttr attrs[4] = {cudaMemPoolAttrUsedMemCurrent, cudaMemPoolAttrUsedMemHigh,
+                                      cudaMemPoolAttrReservedMemCurrent, cudaMemPoolAttrReservedMemHigh};
+    for (int i = 0; i < 4; ++i) {
+        uint64_t v = 0;
+        if (cudaMemPoolGetAttribute(pool, attrs[i], &v) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return PLB_ERR_CUDA;
+        }
+        out[i] = (int64_t)v;
+    }
+    if (reset) {  // high marks can only be set to 0, which restarts them from the current use
+        uint64_t zero = 0;
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess ||
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReservedMemHigh, &zero) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return PLB_ERR_CUDA;
+        }
+    }
+    return PLB_OK;
+}

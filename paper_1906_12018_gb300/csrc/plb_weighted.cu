@@ -562,6 +562,8 @@ int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_
     if (status != PLB_OK) return status;
 
     // ------------------------------------------------------------ finalize
+    // the round buffers go back to the pool before the label set is allocated
+    pool.release_all_except({loff[cur], lent[cur], inv, tmp64, scan_scr, ctr});
     cudaEvent_t f0 = tm.on ? tm.mark() : nullptr;
     plb_labels* L = new plb_labels();
     auto fail = [&](int code) {

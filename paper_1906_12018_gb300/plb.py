@@ -186,6 +186,8 @@ def _lib():
     lib.plb_degree_order.restype = I
     lib.plb_release_cached_memory.argtypes = []
     lib.plb_release_cached_memory.restype = I
+    lib.plb_memory_stats.argtypes = [P, I]
+    lib.plb_memory_stats.restype = I
     lib.plb_degree_order_noalloc.argtypes = [ctypes.POINTER(CSR), P, P]
     lib.plb_degree_order_noalloc.restype = I
     lib.plb_strerror.argtypes = [I]
@@ -204,7 +206,7 @@ def exported_symbols() -> list[str]:
             "plb_query_batch",
             "plb_query_directed", "plb_query_multi",
             "plb_labels_view", "plb_labels_stats", "plb_labels_bytes", "plb_labels_free", "plb_release_cached_memory",
-            "plb_degree_order",
+            "plb_memory_stats", "plb_degree_order",
             "plb_degree_order_noalloc", "plb_strerror", "plb_last_error", "plb_version"]
 
 
@@ -465,6 +467,15 @@ def degree_order_noalloc(row_ptr: torch.Tensor, out: torch.Tensor | None = None,
 def release_cached_memory():
     """Return the library's cached, unused device memory to the driver."""
     _check(_lib().plb_release_cached_memory(), "plb_release_cached_memory")
+
+
+def memory_stats(reset: bool = False) -> dict:
+    """Device bytes of the library's pool on the current device: in use now,
+    the most in use at once since the last reset, reserved now and the most
+    reserved.  reset=True restarts the high marks after reading them."""
+    out = (ctypes.c_int64 * 4)()
+    _check(_lib().plb_memory_stats(ctypes.cast(out, ctypes.c_void_p), 1 if reset else 0), "plb_memory_stats")
+    return {"used": out[0], "used_high": out[1], "reserved": out[2], "reserved_high": out[3]}
 
 
 def version() -> int:

@@ -35,9 +35,18 @@ import numpy as np
 LABELS_LOG_COEF = (-0.6997, 0.3050, 0.7563)  # log(labels/n) = a + b log n + c log(nnz/2n)
 LABEL_SAFETY = 1.5
 # Device bytes per final label at a build's peak (label buffers of both
-# parities, the probe tables, the output arrays): the R-MAT scale-22 build
-# peaked at 59.
+# parities, the probe tables, the frontier buffers): the R-MAT scale-22 build
+# peaks at 74.8 GB, 38 bytes per label beyond its per-vertex and per-arc
+# buffers (measured with plb_memory_stats).
 BUILD_BYTES_PER_LABEL = 64
+# Resident blocks of the block tier (152 SMs x 3), each holding one n-word
+# row of the labels it accepts for a vertex.
+GATHER_BLOCKS = 456
+# Per-vertex device bytes of a build's round state: rank inverse and CSR
+# offsets, label and frontier offsets (two parities), lists, bounds and
+# cursors, the 224-byte top-hub masks, probe-index offsets and descriptors,
+# check records and the row-sort scratch (8 rows of the next power of two).
+BUILD_BYTES_PER_VERTEX = 440
 
 
 def estimated_labels(n: int, nnz: int) -> float:
@@ -54,12 +63,13 @@ def estimated_labels(n: int, nnz: int) -> float:
 
 def build_footprint(n: int, nnz: int) -> int:
     """Device bytes a build of this graph is expected to hold at its peak:
-    inputs (8(n+1) + 4 nnz + 4n), rank-space copy, frontier and tier buffers
-    (about 12 bytes per arc and 64 per vertex), the 224-byte top-hub row per
-    vertex, and BUILD_BYTES_PER_LABEL per estimated label (with the safety
-    factor)."""
+    inputs (8(n+1) + 4 nnz + 4n), the rank-space CSR and first frontier
+    buffers (12 bytes per arc), the round state (BUILD_BYTES_PER_VERTEX and
+    the block tier's accepted rows, 4 GATHER_BLOCKS bytes per vertex), 1 MiB
+    of fixed scratch, and BUILD_BYTES_PER_LABEL per estimated label (with the
+    safety factor)."""
     inputs = 8 * (n + 1) + 4 * nnz + 4 * n
-    work = 12 * nnz + 64 * n + 224 * n
+    work = 12 * nnz + (BUILD_BYTES_PER_VERTEX + 4 * GATHER_BLOCKS) * n + (1 << 20)
     labels = BUILD_BYTES_PER_LABEL * LABEL_SAFETY * estimated_labels(n, nnz)
     return int(inputs + work + labels)
 

@@ -3,6 +3,7 @@ compare GPU label sets with oracle label sets."""
 import numpy as np
 import torch
 
+from paper_1906_12018_gb300 import graphs as G
 from paper_1906_12018_gb300 import plb
 
 
@@ -38,3 +39,21 @@ def gpu_query(lab, pairs):
     out = lab.query(p)
     torch.cuda.synchronize()
     return out.cpu().numpy()
+
+
+def build_peak(g):
+    """Device bytes of the library's pool around one build of g: peak (the
+    most held during the build above what was held before), kept (held with
+    the label set alive), labels (the set's own bytes), left (held after the
+    set is freed) and inputs (the caller's CSR and order, outside the pool)."""
+    rp, col, o = to_device(g, G.degree_order(g))
+    torch.cuda.synchronize()
+    before = plb.memory_stats(reset=True)
+    lab = plb.build(rp, col, o)
+    torch.cuda.synchronize()
+    after = plb.memory_stats()
+    labels = lab.nbytes()
+    lab.free()
+    freed = plb.memory_stats()
+    return {"peak": after["used_high"] - before["used"], "kept": after["used"] - before["used"], "labels": labels,
+            "left": freed["used"] - before["used"], "inputs": rp.numel() * 8 + col.numel() * 4 + o.numel() * 4}

@@ -14,7 +14,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle as O  # noqa: E402
-from gpu_util import gpu_build, gpu_query  # noqa: E402
+from gpu_util import build_peak, gpu_build, gpu_query  # noqa: E402
 from paper_1906_12018_gb300 import graphs as G  # noqa: E402
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -38,6 +38,17 @@ def test_rmat22_size(rmat22):
     g, order, lab = rmat22
     assert (g.n, g.m) == (2394833, 64152981)
     assert lab.total == 1799946086
+
+
+def test_rmat22_build_peak_within_the_admission_footprint(rmat22):
+    """The serving loop admits a build by its footprint model; on the
+    largest graph the machine's measured peak stays inside it."""
+    from paper_1906_12018_gb300.serve import build_footprint
+
+    g, _, _ = rmat22
+    m = build_peak(g)
+    assert m["left"] == 0
+    assert 0 < m["peak"] <= build_footprint(g.n, g.nnz) - m["inputs"], (m, build_footprint(g.n, g.nnz))
 
 
 def stratified_rows(g, order, per=32, seed=22):
