@@ -8,7 +8,7 @@
 namespace plb {
 
 int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
-               const plb_options& o, cudaStream_t s, plb_labels** out);
+               const plb_options& o, cudaStream_t s, plb_labels** out, int64_t max_part_n);
 int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
                         const plb_options& o, cudaStream_t s, plb_labels** out_in, plb_labels** out_out);
 int build_weighted_core(const int64_t* row_ptr, const int32_t* col, const uint8_t* wt, const int32_t* order,
@@ -162,7 +162,7 @@ int plb_build(const plb_csr* g, const int32_t* vertex_order, const plb_options* 
     cudaStream_t s = (cudaStream_t)stream;
     (void)cudaGetLastError();
     if (g->n == 0) return empty_labels(out, s);
-    return plb::build_core(g->row_ptr, g->col, vertex_order, g->n, g->nnz, o, s, out);
+    return plb::build_core(g->row_ptr, g->col, vertex_order, g->n, g->nnz, o, s, out, g->n);
 }
 
 int plb_build_directed(const plb_csr* g, const int32_t* vertex_order, const plb_options* opt, plb_stream stream,
@@ -247,7 +247,9 @@ static int build_union(const plb_csr* gs, const int32_t* const* orders, int64_t 
         return PLB_ERR_CUDA;
     }
     plb_labels* U = nullptr;
-    int st = N > 0 ? plb::build_core(U_off, U_col, U_ord, N, E, o, s, &U) : empty_labels(&U, s);
+    int64_t max_part = 1;  // a vertex accepts hubs of its own graph only
+    for (int64_t i = 0; i < k; ++i) max_part = std::max<int64_t>(max_part, gs[i].n);
+    int st = N > 0 ? plb::build_core(U_off, U_col, U_ord, N, E, o, s, &U, max_part) : empty_labels(&U, s);
     if (st != PLB_OK) {
         cleanup();
         return st;

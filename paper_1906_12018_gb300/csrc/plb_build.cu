@@ -18,9 +18,11 @@ void set_last_error(cudaError_t e, int line) {
 }
 
 // Core build on a validated-or-trusted CSR.  Returns a status; on success
-// *out holds the labels (rows by original id).
+// *out holds the labels (rows by original id).  max_part_n: the most vertices
+// of one graph when the CSR is a disjoint union (else n); a vertex's label
+// holds at most that many hubs, which sizes the block tier's accepted rows.
 int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order, int64_t n, int64_t nnz,
-               const plb_options& o, cudaStream_t s, plb_labels** out) {
+               const plb_options& o, cudaStream_t s, plb_labels** out, int64_t max_part_n) {
 #define PLB_CK(x)                                            \
     do {                                                     \
         const cudaError_t plb_e_ = (x);                      \
@@ -236,7 +238,8 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     PLB_CK(cudaFuncSetAttribute(k_sort_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(16384 * sizeof(uint32_t))));
     // block tier: per-block buffer of accepted hubs (at most v < n per vertex)
-    uint32_t* gacc = pool.alloc<uint32_t>((int64_t)grid_b * std::max<int64_t>(n, 1));
+    const int64_t acc_words = std::max<int64_t>(std::min<int64_t>(n, max_part_n), 1);
+    uint32_t* gacc = pool.alloc<uint32_t>((int64_t)grid_b * acc_words);
     // per-vertex check records (row bounds and probe-table descriptor), packed before each gather
     uint4* hrec = pool.alloc<uint4>(std::max<int64_t>(n, 1));
     PLB_ALLOC_OK();
@@ -268,7 +271,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         p.top_h = top;
         p.hrec_h = hrec;
         p.gscratch = gacc;
-        p.gscratch_words = std::max<int64_t>(n, 1);
+        p.gscratch_words = acc_words;
         p.rbound = rbound;
         p.stage_ratio = o.warp_stage_ratio;
         p.count_check = o.profile != 0;
