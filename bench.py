@@ -434,12 +434,18 @@ def batch_report(args, steps: int, warmup: int, cpu: bool) -> dict:
     t_loop = min(timed(loop) for _ in range(2))
     t_def = min(timed(batch(None)) for _ in range(max(steps, 1)))  # the batch API's defaults
     t_tuned = min(timed(batch(tuned)) for _ in range(max(steps, 1)))
+    # the library pool's high mark over one tuned batched build
+    torch.cuda.synchronize()
+    mem0 = plb.memory_stats(reset=True)
+    timed(batch(tuned))
+    peak = plb.memory_stats()["used_high"] - mem0["used"]
     rep = {"workload": f"batch{k}", "graphs": k, "n": sum(g.n for g in gs), "m": m,
            "value": m / t_tuned, "unit": "edges/s", "ms": 1e3 * t_tuned,
            "one_graph_at_a_time": {"value": m / t_loop, "ms": 1e3 * t_loop},
            "batched_default": {"value": m / t_def, "ms": 1e3 * t_def, "use_graph": 1},
            "batched_tuned": {"value": m / t_tuned, "ms": 1e3 * t_tuned, "options": autotune.as_dict(tuned)},
-           "speedup_vs_one_at_a_time": t_loop / t_tuned, "autotune": tune_report}
+           "speedup_vs_one_at_a_time": t_loop / t_tuned, "autotune": tune_report,
+           "build_peak_bytes": peak}
     gold = os.path.join(ROOT, "tests", "golden", "batch2000_labels.json")
     if not args.no_parity_check and k == 2000 and os.path.exists(gold):
         sys.path.insert(0, os.path.dirname(gold))
