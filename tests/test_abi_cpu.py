@@ -59,6 +59,7 @@ def test_host_only_entry_points(lib):
     assert lib.plb_build(ctypes.byref(g), 1, None, None, ctypes.byref(h)) == plb.PLB_ERR_TOO_LARGE
     assert lib.plb_query_batch(None, None, 1, None, None) == plb.PLB_ERR_INVALID
     assert lib.plb_labels_free(None) == 0
+    assert lib.plb_memory_stats(None, 0) == plb.PLB_ERR_INVALID
 
 
 def test_struct_layouts_match_header():
