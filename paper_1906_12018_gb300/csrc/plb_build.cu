@@ -237,6 +237,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
     PLB_ALLOC_OK();
     PLB_CK(cudaFuncSetAttribute(k_sort_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(16384 * sizeof(uint32_t))));
+    PLB_CK(cudaFuncSetAttribute(k_sort_rows_radix, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortRadixSmemBytes));
     // block tier: per-block buffer of accepted hubs (at most v < n per vertex)
     const int64_t acc_words = std::max<int64_t>(std::min<int64_t>(n, max_part_n), 1);
     uint32_t* gacc = pool.alloc<uint32_t>((int64_t)grid_b * acc_words);
@@ -361,8 +362,7 @@ int build_core(const int64_t* row_ptr, const int32_t* col, const int32_t* order,
         k_next_active<<<gflat, kFlatThreads, 0, s>>>(loff[c], fse[x], n, tmp64, A, ctr);
         // sort the new frontier rows (appended unsorted by the gather/prune kernels)
         k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(fse[x], fhub[x], A, U, 1, ctr, big, giant);
-        k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(fse[x], fhub[x], big, &ctr->nBig, nullptr,
-                                                                        0, ctr);
+        k_sort_rows_radix<<<sms, 1024, kSortRadixSmemBytes, s>>>(fse[x], fhub[x], big, &ctr->nBig, ctr);
         k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(fse[x], fhub[x], giant, &ctr->nGiant,
                                                                             sortscr, sort_words, ctr);
         cudaError_t e = exclusive_scan_i64(tmp64, loff[x], n, scan_scr, s, skip);

@@ -245,6 +245,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
     PLB_CK(cudaFuncSetAttribute(k_gp_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b_smem));
     PLB_CK(cudaFuncSetAttribute(k_sort_rows_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(16384 * sizeof(uint32_t))));
+    PLB_CK(cudaFuncSetAttribute(k_sort_rows_radix, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortRadixSmemBytes));
     int occ_w = 1, occ_b = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_gp_warp, kGpWarpThreads, w_smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_gp_block, bthr, b_smem);
@@ -324,8 +325,7 @@ int build_directed_core(const int64_t* row_ptr, const int32_t* col, const int32_
         const int c = S.cur, x = c ^ 1;
         k_next_active<<<gflat, kFlatThreads, 0, s>>>(S.loff[c], S.fse[x], n, tmp64, S.A, S.ctr);
         k_sort_rows_warp<<<sms * 8, 256, 0, s>>>(S.fse[x], S.fhub[x], S.A, S.U, 1, S.ctr, big, giant);
-        k_sort_rows_block<<<sms * 2, 1024, 16384 * sizeof(uint32_t), s>>>(S.fse[x], S.fhub[x], big, &S.ctr->nBig,
-                                                                        nullptr, 0, S.ctr);
+        k_sort_rows_radix<<<sms, 1024, kSortRadixSmemBytes, s>>>(S.fse[x], S.fhub[x], big, &S.ctr->nBig, S.ctr);
         k_sort_rows_block<<<sort_blocks, 1024, 16384 * sizeof(uint32_t), s>>>(S.fse[x], S.fhub[x], giant,
                                                                             &S.ctr->nGiant, sortscr, sort_words,
                                                                             S.ctr);

@@ -598,6 +598,113 @@ __global__ void __launch_bounds__(1024) k_sort_rows_block(const uint64_t* fse_ne
     }
 }
 
+// Rows of kWarpSortMax < c <= kBlockSortSmem entries (the list k_sort_rows_warp
+// makes): one block of kRadixThreads per row, an LSD radix sort in shared
+// memory on the three 8-bit digits of a hub rank (below 2^24).  Each pass is
+// stable: warp w owns the w-th
+// contiguous chunk of the row and reads it 32 entries at a time in order;
+// lanes with equal digits find one another with __match_any_sync.  A count
+// pass fills a (digit, warp) histogram, its exclusive scan in digit-major
+// order gives every warp its first slot per digit, and a scatter pass writes
+// each entry at that slot plus its rank among the earlier equal digits.
+constexpr int kRadixThreads = 1024;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixBins = 256;
+static_assert(kRadixBins * kRadixWarps % kRadixThreads == 0, "histogram scan: whole entries per thread");
+static_assert(kSortRadixSmemBytes == (2 * kBlockSortSmem + (kRadixBins + 1) * kRadixWarps) * (int)sizeof(uint32_t),
+              "launch size of k_sort_rows_radix");
+
+__global__ void __launch_bounds__(kRadixThreads) k_sort_rows_radix(const uint64_t* fse_new, uint32_t* fhub_new,
+                                                                  const int32_t* big, const int* nbig,
+                                                                  const RoundCounters* ctr) {
+    extern __shared__ uint32_t sbuf[];
+    uint32_t* buf0 = sbuf;                                                     // kBlockSortSmem
+    uint32_t* buf1 = sbuf + kBlockSortSmem;                                    // kBlockSortSmem
+    // (digit, warp) counts, warp-major with a padded row: the digits a warp's
+    // lanes touch at once fall in different banks
+    int* hist = reinterpret_cast<int*>(sbuf + 2 * kBlockSortSmem);             // [kRadixWarps][kRadixBins + 1]
+    auto hidx = [](uint32_t dg, int ww) { return ww * (kRadixBins + 1) + (int)dg; };
+    __shared__ int wtot[kRadixWarps];
+    constexpr int kPer = kRadixBins * kRadixWarps / kRadixThreads;            // histogram entries per thread
+    if (ctr->done) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nBig = *nbig;
+    for (int i = blockIdx.x; i < nBig; i += gridDim.x) {
+        const uint64_t f = fse_new[big[i]];
+        const int c = min((int)fcount(f), kBlockSortSmem);  // (the list holds rows of at most kBlockSortSmem)
+        uint32_t* row = fhub_new + fstart(f);
+        constexpr int passes = 3;  // hub ranks below 2^24
+        for (int j = threadIdx.x; j < c; j += kRadixThreads) buf0[j] = row[j];
+        const int chunk = (c + kRadixWarps - 1) / kRadixWarps;
+        const int wb = min(c, w * chunk), we = min(c, wb + chunk);
+        uint32_t* src = buf0;
+        uint32_t* dst = buf1;
+        for (int pass = 0; pass < passes; ++pass) {
+            const int shift = 8 * pass;
+            for (int j = threadIdx.x; j < (kRadixBins + 1) * kRadixWarps; j += kRadixThreads) hist[j] = 0;
+            __syncthreads();  // (and the row is loaded)
+            for (int b0 = wb; b0 < we; b0 += 32) {
+                const int j = b0 + lane;
+                const bool in = j < we;
+                const uint32_t dg = in ? (src[j] >> shift) & (kRadixBins - 1) : (uint32_t)kRadixBins;
+                const unsigned peers = __match_any_sync(kFull, dg);
+                if (in && (peers & lt) == 0u) hist[hidx(dg, w)] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            {  // exclusive scan of the histogram in place, in digit-major order
+                int x[kPer], sum = 0;
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const int pos = threadIdx.x * kPer + k;
+                    x[k] = hist[hidx(pos / kRadixWarps, pos % kRadixWarps)];
+                    sum += x[k];
+                }
+                const int incl = warp_incl_scan(sum, lane);
+                if (lane == 31) wtot[w] = incl;
+                __syncthreads();
+                if (w == 0) {
+                    const int t = wtot[lane];
+                    const int ti = warp_incl_scan(t, lane);
+                    __syncwarp();
+                    wtot[lane] = ti - t;
+                }
+                __syncthreads();
+                int run = wtot[w] + incl - sum;
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const int pos = threadIdx.x * kPer + k;
+                    hist[hidx(pos / kRadixWarps, pos % kRadixWarps)] = run;
+                    run += x[k];
+                }
+            }
+            __syncthreads();
+            for (int b0 = wb; b0 < we; b0 += 32) {
+                const int j = b0 + lane;
+                const bool in = j < we;
+                const uint32_t x = in ? src[j] : 0u;
+                const uint32_t dg = in ? (x >> shift) & (kRadixBins - 1) : (uint32_t)kRadixBins;
+                const unsigned peers = __match_any_sync(kFull, dg);
+                const int leader = __ffs(peers) - 1;
+                int base = 0;
+                if (in && lane == leader) base = hist[hidx(dg, w)];
+                base = __shfl_sync(kFull, base, leader);
+                if (in) dst[base + __popc(peers & lt)] = x;
+                __syncwarp();
+                if (in && lane == leader) hist[hidx(dg, w)] = base + __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();  // every warp is done with this pass's histogram and output
+            uint32_t* t = src;
+            src = dst;
+            dst = t;
+        }
+        for (int j = threadIdx.x; j < c; j += kRadixThreads) row[j] = src[j];
+        __syncthreads();
+    }
+}
+
 // Old entries move to their place in the merged row: flat over old entries.
 // A tile of entries that spans at most kMergeRows rows stages those rows'
 // old and new offsets and new-frontier descriptors in shared memory (each

@@ -53,6 +53,11 @@ __global__ void k_next_active(const int64_t* loff, const uint64_t* fse_new, int6
                               RoundCounters* ctr);
 __global__ void k_sort_rows_warp(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* A, const int32_t* U,
                                  int r1_all, RoundCounters* ctr, int32_t* big, int32_t* giant);
+// Dynamic shared memory of k_sort_rows_radix: two row buffers of 16,384
+// entries and a 32-warp x (256 + 1)-digit histogram.
+constexpr int kSortRadixSmemBytes = (2 * 16384 + 257 * 32) * 4;
+__global__ void k_sort_rows_radix(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* big, const int* nbig,
+                                  const RoundCounters* ctr);
 __global__ void k_sort_rows_block(const uint64_t* fse_new, uint32_t* fhub_new, const int32_t* big, const int* nbig,
                                   uint32_t* scratch, int64_t scratch_words, const RoundCounters* ctr);
 __global__ void k_merge_old(const int64_t* loff, const uint32_t* lent, const int64_t* loff_new, uint32_t* lent_new,
