@@ -77,7 +77,7 @@ typedef struct {
     int32_t validate;          /* 1: check CSR and order on the device first (default 1) */
     int32_t warp_label_cap;    /* largest |L(v)| handled one-vertex-per-warp (default 512) */
     int32_t warp_cand_cap;     /* largest unique-candidate count per warp-vertex (default 512) */
-    int32_t block_label_cap;   /* largest |L(v)| the block tier stages in shared memory (default 2048) */
+    int32_t block_label_cap;   /* largest |L(v)| the block tier stages in shared memory (default 512) */
     int32_t block_cand_cap;    /* unique candidates per hub-range pass of the block tier (default 2048) */
     int32_t block_threads;     /* threads of the block tier, 64..256, rounded down to a multiple of 32 (default 256) */
     int32_t use_graph;         /* 1: run the rounds after round 1 as a captured CUDA graph with
