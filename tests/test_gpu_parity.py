@@ -127,6 +127,7 @@ def _bad_build(off, col, order):
 def test_invalid_inputs_rejected():
     ok_off, ok_col = [0, 1, 3, 4], [1, 0, 2, 1]           # path 0-1-2
     assert _bad_build([0, 1, 3, 4], [1, 0, 2, 0], [0, 1, 2]) == plb.PLB_ERR_INVALID   # asymmetric
+    assert _bad_build([0, 1, 2, 3], [1, 0, 0], [0, 1, 2]) == plb.PLB_ERR_INVALID      # asymmetric: arc 2->0 alone
     assert _bad_build([0, 1, 3, 4], [1, 2, 0, 1], [0, 1, 2]) == plb.PLB_ERR_INVALID   # unsorted row
     assert _bad_build([0, 2, 4, 5], [0, 1, 0, 2, 1], [0, 1, 2]) == plb.PLB_ERR_INVALID  # self-loop
     assert _bad_build([0, 1, 3, 4], [1, 0, 7, 1], [0, 1, 2]) == plb.PLB_ERR_INVALID   # out of range
