@@ -367,6 +367,7 @@ int64_t plb_labels_bytes(const plb_labels* L) { return L ? L->bytes : 0; }
 
 int plb_labels_free(plb_labels* L) {
     if (!L) return PLB_OK;
+    (void)cudaGetLastError();  // report this call's failures (a sticky error shows again below)
     cudaDeviceSynchronize();
     if (L->shared) {
         auto* sh = static_cast<plb::Shared*>(L->shared);

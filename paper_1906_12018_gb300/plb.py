@@ -316,8 +316,8 @@ class Labels:
 
     def free(self):
         if self._h:
-            _lib().plb_labels_free(self._h)
-            self._h = ctypes.c_void_p()
+            h, self._h = self._h, ctypes.c_void_p()  # never freed twice, even if the call fails
+            _check(_lib().plb_labels_free(h), "plb_labels_free")
 
     def __del__(self):
         try:
