@@ -142,3 +142,34 @@ def test_binding_checks_buffer_sizes_before_calling_the_library(monkeypatch):
     plb.degree_order_noalloc(rp, out=torch.empty(10, dtype=i32))
     plb.query_multi([lab], torch.zeros(4, dtype=i32), torch.zeros(8, dtype=i32), out=torch.empty(4, dtype=i32))
     assert calls == ["plb_degree_order_noalloc", "plb_query_multi"]
+
+
+def test_free_reports_a_failed_free_once(monkeypatch):
+    """Labels.free passes the library's status on (PLBError) and clears the
+    handle first: a second free, or the destructor, calls nothing."""
+    from paper_1906_12018_gb300 import plb
+
+    calls = []
+
+    class FakeLib:
+        def plb_labels_free(self, h):
+            calls.append(h.value)
+            return plb.PLB_ERR_CUDA
+
+        def plb_strerror(self, code):
+            return b"CUDA error"
+
+        def plb_last_error(self):
+            return b""
+
+    monkeypatch.setattr(plb, "_lib", lambda: FakeLib())
+    lab = object.__new__(plb.Labels)
+    lab._h = ctypes.c_void_p(1234)
+    with pytest.raises(plb.PLBError) as e:
+        lab.free()
+    assert e.value.code == plb.PLB_ERR_CUDA
+    lab.free()
+    lab.__del__()
+    assert calls == [1234]
+    with pytest.raises(RuntimeError):
+        lab.handle
