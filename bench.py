@@ -260,13 +260,14 @@ def oracle_full_run(name: str) -> dict | None:
             rec = json.load(f).get(name)
         if rec:
             return {"labels": int(rec["labels"]), "seconds": rec.get("pll_seconds"),
-                    "host": {"machine": rec.get("machine")}}
+                    "host": {"machine": rec.get("machine")}, "max_dist": rec.get("max_dist")}
     except (OSError, ValueError):
         pass
     try:
         with open(os.path.join(ROOT, "tests", "golden", f"{name}_labels.json")) as f:
             rec = json.load(f)
-        return {"labels": int(rec["labels"]), "seconds": rec.get("pll_seconds"), "host": rec.get("host")}
+        return {"labels": int(rec["labels"]), "seconds": rec.get("pll_seconds"), "host": rec.get("host"),
+                "max_dist": rec.get("max_dist")}
     except (OSError, ValueError, KeyError):
         return None
 
@@ -332,14 +333,20 @@ def run_reference(args):
             samples.append(s)
     v = statistics.median(s["value"] for s in samples)
     sec = statistics.median(s["sample_seconds"] for s in samples)
+    full = oracle_full_run(args.workload)
+    config = workload_config(args.workload, g, total)
+    if full and full.get("max_dist") is not None:  # the same keys as the main line's config
+        config = dict(config, rounds=int(full["max_dist"]) + 1,
+                      parallelism="replicas" if world > 1 else "single", batch_hubs=args.batch_hubs)
     line = {"metric": "labeling edges/sec", "value": v, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * sec, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": workload_config(args.workload, g, total), "impl": "reference",
+            "ms_per_step_is": "the timed oracle sample of one step (a prefix of the build), not a whole build",
+            "estimated_ms_per_build": 1000 * g.m / v if v else None,
+            "config": config, "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "edges/s", "host": host_cpu(),
                              "method": samples[0]["method"], "sample": samples[0]["sample"]},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    full = oracle_full_run(args.workload)
     if full and full.get("seconds"):
         line["cpu_full_run"] = dict(full, value=g.m / float(full["seconds"]), unit="edges/s")
     print(json.dumps(line), flush=True)
