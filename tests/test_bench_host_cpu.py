@@ -95,3 +95,25 @@ def test_traffic_guard_covers_the_round1_kernels():
     sec = bench.round1_section()
     assert "k_round1_count" in sec and "k_round1(" in sec and "tile_rows" in sec
     assert "k_merge_new" not in sec and "k_index_build" not in sec
+
+
+def test_reference_arm_line_matches_the_main_line_config(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line whose config carries
+    the main line's keys (rounds from the full oracle run: rmat12's largest
+    distance is 3) and says what its ms_per_step times."""
+    import argparse
+    import json
+
+    import bench
+
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    args = argparse.Namespace(workload="rmat12", steps=1, warmup=0, cpu_seconds=0.2, batch_hubs=0)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    cfg = line["config"]
+    assert cfg["workload"] == "rmat12" and cfg["labels"] == 82231
+    assert cfg["rounds"] == 4 and cfg["parallelism"] == "single" and cfg["batch_hubs"] == 0
+    assert "sample" in line["ms_per_step_is"] and line["estimated_ms_per_build"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
